@@ -1,0 +1,401 @@
+#!/usr/bin/env python3
+"""Benchmark of the DVNR hot path (arXiv 2304.10516) on GB300.
+
+Metric: INR training samples/s (and decode samples/s) at equal PSNR to the
+plain FP32 path. One *step* is one training iteration of the whole hot path
+over one batch: sampling, trilinear targets, hash-grid encoding, MLP forward,
+L1 loss, backward, gradient scatter and Adam (plus, reported beside it,
+decoding and ray-marching of the trained model).
+
+Workload (default): the 256^3 spectral-field model -- hash grid L=16, F=2,
+T=2^19, N_min=16, b=1.38, MLP 32->64->64->64->1, batch 2^18 samples/step.
+Inputs are seeded synthetic fields resident in HBM before the timed region.
+The per-step working set (tables, gradients, Adam moments, volume) is larger
+than the 129 MB L2, so no explicit flush is needed between steps.
+
+Under torchrun (N > 1) every rank trains its own partition model with no
+exchange between ranks (the paper's model parallelism, Sec. 3.1): weak
+scaling, timed with a barrier and the max over ranks.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this
+tier) on the same workload, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "spectral256": dict(desc="256^3 spectral k^-5/3 field, L=16 F=2 T=2^19 N0=16 b=1.38, "
+                             "MLP 32-64-64-64-1, batch 2^18",
+                        shape=(256, 256, 256), seed=1002, L=16, F=2, log2T=19, base=16, growth=1.38,
+                        width=64, hidden=3, batch=1 << 18, steps_full=2000, lam=0.0, lr=1e-2),
+    "blobs64": dict(desc="64^3 Gaussian blobs, L=8 F=2 T=2^15 N0=4 b=1.5, MLP 16-32-32-1, batch 4096",
+                    shape=(64, 64, 64), seed=1001, L=8, F=2, log2T=15, base=4, growth=1.5,
+                    width=32, hidden=2, batch=4096, steps_full=200, lam=0.0, lr=1e-2),
+}
+
+SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="spectral256", choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default="auto", choices=["auto", "fp16", "fp32"])
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the e2e, decode, render and CPU-baseline legs")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks ---
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="dvnr_clocks_", suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={SMI_FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------- algorithmic bytes/flops ---
+def kernel_bytes(name, w, n_params, batch):
+    """Algorithmic bytes of one launch of kernel `name` (per-unit figures x
+    units per launch; the figures are derived in the design doc)."""
+    L, F, W, H = w["L"], w["F"], w["width"], w["hidden"]
+    D = L * F
+    if name == "adam":
+        return 34 * n_params  # read g, theta, m, v; write theta, m, v, fp16 copy, zeroed g
+    if name == "train_fused_fp16":
+        # per sample: 8 fp32 volume reads, 8 fp16 corner reads and 8 fp32 corner
+        # gradient read-modify-writes per feature and level
+        return batch * (8 * 4 + L * 8 * F * 2 + L * 8 * F * 4)
+    if name == "fp32_sample_encode":
+        return batch * (8 * 4 + L * 8 * F * 4 + D * 4 + 12 + 4)
+    if name == "fp32_scatter":
+        return batch * (L * 8 * F * 4 + D * 4 + 12)
+    return None
+
+
+# ------------------------------------------------------------ our arm -------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2304_10516_gb300 import _abi as A
+    from paper_2304_10516_gb300 import model as dv
+    from paper_2304_10516_gb300 import volumes
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOADS[args.workload]
+    lib = A.load()
+    prec = args.precision
+    if prec == "auto":
+        prec = "fp16"
+    precision = A.DVNR_FP16 if prec == "fp16" else A.DVNR_FP32
+
+    vol_np = volumes.spectral(w["shape"], seed=w["seed"] + rank) if args.workload == "spectral256" \
+        else volumes.blobs(w["shape"][0], seed=w["seed"] + rank)
+    vol = torch.from_numpy(vol_np).to(dev)
+    nz, ny, nx = vol_np.shape
+    enc = dv.EncodingConfig(w["L"], w["F"], w["log2T"], w["base"], w["growth"])
+    mlp = dv.MLPConfig(w["width"], w["hidden"])
+
+    def new_model(seed):
+        return dv.Model((0, 0, 0), (nx, ny, nz), 0, enc, mlp, seed=seed)
+
+    def cfg(steps, prec_code=precision):
+        return dv.TrainConfig(batch=w["batch"], steps=steps, lr=w["lr"], lambda_bnd=w["lam"],
+                              precision=prec_code, seed=7 + rank)
+
+    model = new_model(100 + rank)
+    stream = torch.cuda.current_stream()
+    gpu_index = local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0
+    clocks = ClockSampler(gpu_index)
+    # warm-up (untimed)
+    dv.train([model], [vol], cfg(max(args.warmup, 3)), sync=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lib.dvnr_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dv.train([model], [vol], cfg(args.steps), stream=stream, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.dvnr_launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    samples = w["batch"] * args.steps * world
+    value = samples / (ms / 1e3)
+    result = {
+        "metric": "INR train samples/s and decode samples/s at equal PSNR vs plain FP32 path",
+        "value": value, "unit": "train samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f16" if precision == A.DVNR_FP16 else "f32",
+        "data": "synthetic (seeded random-phase k^-5/3 spectral field)",
+        "config": {"workload": w["desc"], "global_batch": w["batch"] * world,
+                   "parallelism": f"{world} independent partition models (no exchange)",
+                   "precision": prec, "l2": "working set > L2 (no flush needed)"},
+        "clocks": clk, "gpu_launches": int(launches),
+    }
+    if rank != 0:
+        return None
+    if args.no_extras:
+        return result
+
+    # ---- dominant-kernel roofline: per-launch CUDA events on the launching stream
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    A.call("dvnr_profile_enable", 1)
+    nprof = min(args.steps, 50)
+    dv.train([model], [vol], cfg(nprof), sync=True)
+    import ctypes as C
+
+    kern = {}
+    names = ["train_fused_fp16", "adam", "minmax", "fp32_sample_encode", "fp32_gemm",
+             "fp32_out_loss", "fp32_scatter"]
+    for n in names:
+        tms, cnt = C.c_double(), C.c_int64()
+        A.call("dvnr_profile_read", n.encode(), C.byref(tms), C.byref(cnt))
+        if cnt.value:
+            kern[n] = (tms.value, cnt.value)
+    A.call("dvnr_profile_enable", 0)
+    total = sum(v[0] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k][0])
+    dms, dcnt = kern[dom]
+    byt = kernel_bytes(dom, w, model.n_params, w["batch"])
+    ach = byt / (dms / dcnt / 1e3) / 1e9 if byt else None
+    result["roofline"] = {
+        "kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+        "frac": (ach / hbm_peak) if ach else None, "traffic": None,
+        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+        "avg_launch_ms": dms / dcnt,
+        "share": {k: round(v[0] / total, 4) for k, v in kern.items()},
+    }
+
+    # ---- decode and render of the trained model
+    torch.cuda.synchronize()
+    ex, ey, ez = nx, ny, nz
+    out = torch.empty((ez, ey, ex), device=dev)
+    model.decode_grid(out)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    d0.record(stream)
+    for _ in range(reps):
+        model.decode_grid(out)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dec_ms = d0.elapsed_time(d1) / reps
+    result["decode"] = {"value": ex * ey * ez / (dec_ms / 1e3), "unit": "decode samples/s",
+                        "ms": dec_ms, "points": ex * ey * ez}
+    tf = dv.make_tf(alpha_max=0.05)
+    img = dv.render([model], tf, 1024, 1024, 512)
+    torch.cuda.synchronize()
+    A.call("dvnr_profile_enable", 1)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    dv.render([model], tf, 1024, 1024, 512, out=img)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    tms, cnt = C.c_double(), C.c_int64()
+    A.call("dvnr_profile_read", b"render", C.byref(tms), C.byref(cnt))
+    A.call("dvnr_profile_enable", 0)
+    result["render"] = {"value": 1024 * 1024 * 512 / (tms.value / 1e3), "unit": "ray samples/s",
+                        "march_ms": tms.value, "decode_plus_march_ms": r0.elapsed_time(r1),
+                        "image": [1024, 1024], "samples_per_ray": 512}
+
+    # ---- end to end through the public API: host volume -> train -> loss
+    pinned = torch.from_numpy(vol_np).pin_memory()
+    dvol = torch.empty_like(vol)
+
+    def e2e(prec_code, reps):
+        m = new_model(100 + rank)
+        w0 = m.get_weights()
+        res = []
+        for r in range(reps):
+            if r:
+                m.set_weights(w0)  # same initial weights and fresh optimiser state
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dvol.copy_(pinned, non_blocking=True)
+            loss = dv.train([m], [dvol], cfg(w["steps_full"], prec_code), sync=True)
+            t1 = time.perf_counter()
+            res.append(t1 - t0)
+        dec = m.decode_grid()
+        sse, mx = dv.error_stats(dec, vol)
+        mse = sse / vol.numel()
+        m.close()
+        return min(res), 10 * math.log10(1.0 / mse), mx, loss[0]
+
+    clocks_e2e = ClockSampler(gpu_index)
+    t_mp, psnr_mp, mx_mp, loss_mp = e2e(precision, 2)
+    t_32, psnr_32, mx_32, loss_32 = e2e(A.DVNR_FP32, 1)
+    result["clocks_e2e"] = clocks_e2e.stop()
+    steps_full = w["steps_full"]
+    result["e2e"] = {"value": steps_full * w["batch"] / t_mp, "unit": "train samples/s",
+                     "h2d_bytes_per_step": int(vol.numel() * 4), "d2h_bytes_per_step": 4,
+                     "step": f"upload volume, {steps_full} training iterations, read loss"}
+    result["psnr"] = {"path": psnr_mp, "fp32_path": psnr_32, "delta_db": psnr_mp - psnr_32,
+                      "max_abs": mx_mp, "fp32_max_abs": mx_32, "steps": steps_full}
+    result["fp32_path"] = {"value": steps_full * w["batch"] / t_32, "unit": "train samples/s",
+                           "speedup": t_32 / t_mp}
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
+    result["cpu_baseline"] = cpu_baseline(w, vol_np)
+    return result
+
+
+def cpu_baseline(w, vol_np, budget_s=12.0):
+    import oracle as orc
+
+    oc = orc.Config(w["L"], w["F"], w["log2T"], w["base"], w["growth"], w["width"], w["hidden"])
+    th = orc.init_params(oc, 100)
+    m1, m2 = np.zeros_like(th), np.zeros_like(th)
+    batch = min(w["batch"], 1 << 15)
+    tc = orc.TrainConfig(batch=batch, lr=w["lr"], seed=7)
+    st = orc.State()
+    vmin, vmax = float(vol_np.min()), float(vol_np.max())
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        orc.train(oc, tc, st, th, m1, m2, vol_np, vmin, vmax, 1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 50:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": steps * batch / dt, "unit": "train samples/s", "cores": orc.threads(),
+            "kind": "oracle",
+            "sample": f"{steps} FP64 training iterations of the same model at batch {batch} "
+                      f"(Adam over all {oc.n_params} parameters each iteration)"}
+
+
+# ------------------------------------------------------ reference arm ------
+def run_reference(args):
+    import oracle as orc
+
+    from paper_2304_10516_gb300 import volumes
+
+    w = WORKLOADS[args.workload]
+    vol_np = volumes.spectral(w["shape"], seed=w["seed"]) if args.workload == "spectral256" \
+        else volumes.blobs(w["shape"][0], seed=w["seed"])
+    oc = orc.Config(w["L"], w["F"], w["log2T"], w["base"], w["growth"], w["width"], w["hidden"])
+    th = orc.init_params(oc, 100)
+    m1, m2 = np.zeros_like(th), np.zeros_like(th)
+    batch = min(w["batch"], 1 << 13)
+    tc = orc.TrainConfig(batch=batch, lr=w["lr"], seed=7)
+    st = orc.State()
+    vmin, vmax = float(vol_np.min()), float(vol_np.max())
+    orc.train(oc, tc, st, th, m1, m2, vol_np, vmin, vmax, max(args.warmup, 1))
+    t0 = time.perf_counter()
+    orc.train(oc, tc, st, th, m1, m2, vol_np, vmin, vmax, args.steps)
+    dt = time.perf_counter() - t0
+    value = args.steps * batch / dt
+    sample = (f"each step one FP64 training iteration of the same model at batch {batch} "
+              f"(a bounded sample of the {w['batch']}-sample step)")
+    return {
+        "impl": "reference", "metric": "INR train samples/s and decode samples/s at equal PSNR "
+        "vs plain FP32 path", "value": value, "unit": "train samples/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded random-phase k^-5/3 spectral field)",
+        "config": {"workload": w["desc"], "global_batch": batch, "parallelism": "1 CPU process"},
+        "cpu_baseline": {"value": value, "unit": "train samples/s", "cores": orc.threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "train samples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)))
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,275 @@
+/*
+ * dvnr.h -- C ABI of libdvnr.so, the GB300 (sm_103a) implementation of the
+ * hot path of "Distributed Neural Representation for Reactive In Situ
+ * Visualization" (DVNR, arXiv 2304.10516).
+ *
+ * The library trains one implicit neural representation (INR) per box
+ * partition of a volume (Sec. 3.1), with no exchange between partitions, and
+ * decodes and ray-marches the trained models (Sec. 3, Sec. 4.3). Each INR is
+ * a multiresolution hash-grid encoding (Sec. 3, after Mueller et al. 2022)
+ * followed by a small ReLU MLP without biases and with a linear scalar
+ * output (Sec. 3).
+ *
+ * Conventions shared by every call:
+ *  - Device pointers ("_dev") point to memory of the current CUDA device;
+ *    the caller owns them. The library owns model parameters, optimiser
+ *    state and workspaces. Volumes are only borrowed during dvnr_train
+ *    (the paper revokes field access after training, Sec. 4.1).
+ *  - Volumes are float32, x fastest, then y, then z ([z][y][x]).
+ *  - "stream" is a cudaStream_t (NULL = legacy default stream). Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Every call returns a dvnr_status; nothing aborts or traps. On an error
+ *    dvnr_last_error() returns a message (thread-local, valid until the next
+ *    call on the same thread). Argument errors are detected on the host before
+ *    any work is queued. Errors found by kernels (non-finite input, a
+ *    non-finite gradient) are recorded in the model's device state and
+ *    reported by the next synchronising call (dvnr_get_state, or dvnr_train
+ *    with final_loss_host != NULL).
+ *  - The library is compute-only: it uses one GPU and no collectives.
+ *
+ * Fixed-point coordinates: the INR domain of a model is [0,1]^3 spanning the
+ * centres of the first and last stored voxel (ghost layer included). A unit
+ * coordinate u is represented exactly as m / 2^24 with the integer
+ * m in [0, 2^24]; hash indices and trilinear weights are computed from m.
+ */
+#ifndef DVNR_H
+#define DVNR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DVNR_ABI_VERSION 1
+
+typedef struct dvnr_model_s* dvnr_model; /* opaque, library-owned */
+
+typedef enum {
+  DVNR_OK = 0,
+  DVNR_E_INVALID = 1,          /* bad argument (host-side check)            */
+  DVNR_E_OOM = 2,              /* device allocation failed                  */
+  DVNR_E_CUDA = 3,             /* a CUDA runtime call failed                */
+  DVNR_E_NONFINITE_INPUT = 4,  /* NaN/Inf found in a training volume        */
+  DVNR_E_TIMEOUT = 5,          /* a bounded device wait gave up             */
+  DVNR_E_STATE = 6,            /* call not valid in the model's state       */
+  DVNR_E_UNSUPPORTED = 7       /* configuration outside the compiled set    */
+} dvnr_status;
+
+typedef enum { DVNR_FP32 = 0, DVNR_FP16 = 1 } dvnr_precision;
+typedef enum { DVNR_LOSS_L1 = 0, DVNR_LOSS_L2 = 1 } dvnr_loss;
+
+/* Partition box in global voxel indices (Sec. 3.1: each rank owns a box).
+ * Owned voxels are [lo, hi) per axis; the stored block adds `ghost` layers
+ * on every side (Sec. 3.3, one ghost layer), so it has
+ * (hi - lo + 2 ghost) voxels per axis, at least 2.                          */
+typedef struct {
+  int64_t lo[3], hi[3];
+  int32_t ghost;
+} dvnr_box;
+
+/* Hash-grid encoding (Sec. 3, appendix network configs: n_levels,
+ * n_features_per_level, log2_hashmap_size, base_resolution,
+ * per_level_scale). Level l has resolution N_l = floor(base_res growth^l);
+ * it is stored densely when (N_l+1)^3 <= 2^log2_T, else hashed into 2^log2_T
+ * entries with the spatial hash of Mueller et al.
+ * Supported: 1 <= n_levels <= 32, n_features in {1,2,4,8},
+ * 4 <= log2_T <= 24, N_l <= 2^21.                                           */
+typedef struct {
+  int32_t n_levels, n_features, log2_T, base_res;
+  double growth;
+} dvnr_enc_cfg;
+
+/* ReLU MLP (Sec. 3; appendix: n_neurons, n_hidden_layers). n_hidden hidden
+ * layers of `width` units, then one linear output. No biases.
+ * Supported: width in {16, 32, 64}, 1 <= n_hidden <= 8. The FP16 path also
+ * needs n_levels * n_features a multiple of 16 and at most 64.             */
+typedef struct {
+  int32_t width, n_hidden;
+} dvnr_mlp_cfg;
+
+/* Training configuration (Sec. 3.2 batch, Sec. 3.3 lambda/sigma, Sec. 3.6
+ * Adam beta1 = 0.9, beta2 = 0.999, eps = 1e-8, L2 weight decay 1e-9,
+ * boundary weight lambda = 0.15, sigma = 0.005).
+ *   batch          samples per model per step (N_batch), >= 1
+ *   lambda_bnd     fraction of boundary samples, floor(lambda batch)
+ *   sigma_bnd      half-Gaussian spread in unit coordinates, (0, 1]
+ *   precision      DVNR_FP32: plain FP32 SIMT path, one model at a time
+ *                  DVNR_FP16: FP16 tables and MLP operands on tcgen05
+ *                  tensor cores, FP32 accumulation, FP32 master weights and
+ *                  Adam, dynamic loss scaling; all models of the call in one
+ *                  grouped launch per step
+ *   loss           DVNR_LOSS_L1 (paper) or DVNR_LOSS_L2
+ *   growth_interval  FP16 path: finite steps before the loss scale doubles
+ *   steps          iterations to run in this call (>= 0)
+ *   seed           sampling seed; model i of the call uses RNG key
+ *                  (seed, i) -- the Philox counter also carries the model's
+ *                  iteration count, so repeated calls draw fresh samples.   */
+typedef struct {
+  float lr, beta1, beta2, eps, weight_decay;
+  float lambda_bnd, sigma_bnd;
+  int32_t batch, precision, loss, growth_interval;
+  int64_t steps;
+  uint64_t seed;
+} dvnr_train_cfg;
+
+/* Snapshot of a model (read synchronously by dvnr_get_state).              */
+typedef struct {
+  double vmin, vmax;       /* value range of the last training volume (Sec. 4.1) */
+  double loss_scale;       /* FP16 path dynamic loss scale                     */
+  double last_loss;        /* mean loss of the last step                       */
+  int64_t iter;            /* iterations drawn                                  */
+  int64_t adam_t;          /* Adam steps applied                                */
+  int64_t skipped;         /* steps skipped for a non-finite gradient           */
+  int64_t n_enc, n_mlp;    /* parameter counts                                  */
+  int32_t precision;       /* precision used by decode/render                   */
+  int32_t nonfinite_input; /* 1 when the last training volume held NaN/Inf      */
+} dvnr_state_info;
+
+/* Transfer function for dvnr_render: rgb = c0 + (c1 - c0) v and
+ * alpha = alpha_max v, with v = clamp((value - v_lo)/(v_hi - v_lo), 0, 1).  */
+typedef struct {
+  float c0[3], c1[3];
+  float alpha_max, v_lo, v_hi;
+} dvnr_tf;
+
+/* Optional device outputs of dvnr_train_grad (each may be NULL).           */
+typedef struct {
+  float* grad;       /* n_enc + n_mlp: gradient of the mean loss (unscaled)  */
+  float* y;          /* batch: network output in normalised units            */
+  float* target;     /* batch: normalised target                              */
+  float* dx0;        /* batch x (n_levels n_features): dL/d(encoding),        */
+                     /*   unscaled, level-major                               */
+  uint32_t* coords;  /* batch x 3: fixed-point sample coordinates             */
+  float* loss;       /* 1: mean loss of the batch                             */
+} dvnr_step_outputs;
+
+/* ABI version (DVNR_ABI_VERSION of the built library).                     */
+int32_t dvnr_abi_version(void);
+
+/* Message of the last failed call on this thread ("" if none).             */
+const char* dvnr_last_error(void);
+
+/* Create one INR for the partition `box` (Sec. 3.1) on the current device.
+ * Parameters are initialised from `seed` (tables U(-1e-4, 1e-4), MLP
+ * Glorot-uniform; Philox-4x32-10 counter {i_lo, i_hi, 0, 'INIT'},
+ * key = seed), Adam moments are zero, value range [0, 1], precision FP32.
+ * Synchronises the device. Errors: DVNR_E_INVALID (box/config),
+ * DVNR_E_UNSUPPORTED, DVNR_E_OOM, DVNR_E_CUDA.                              */
+dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc,
+                        const dvnr_mlp_cfg* mlp, uint64_t seed,
+                        dvnr_model* out);
+
+/* Free a model (NULL is ignored). Synchronises the model's device.         */
+void dvnr_destroy(dvnr_model m);
+
+/* Parameter counts: tables (n_enc) and MLP weights (n_mlp).                */
+dvnr_status dvnr_param_count(dvnr_model m, int64_t* n_enc, int64_t* n_mlp);
+
+/* Copy the FP32 master parameters to/from host memory (n = n_enc + n_mlp
+ * floats, layout: tables level by level, entries x features with features
+ * contiguous; then W_0 [width x in_dim], W_1..W_{H-1} [width x width],
+ * w_out [width], each row-major [out][in]). set_weights also refreshes the
+ * FP16 copy and resets the optimiser state (moments, step counts, loss
+ * scale). Both synchronise.                                                 */
+dvnr_status dvnr_get_weights(dvnr_model m, float* host, int64_t n);
+dvnr_status dvnr_set_weights(dvnr_model m, const float* host, int64_t n);
+
+/* Weight caching (Sec. 3.5): initialise `dst` from `src` (same encoding and
+ * MLP configuration), copying parameters and value range and resetting
+ * dst's Adam moments and step counts. Asynchronous on `stream`.            */
+dvnr_status dvnr_copy_weights(dvnr_model dst, dvnr_model src, void* stream);
+
+/* Select the precision used by decode and render (training sets it to the
+ * training precision). Switching to FP16 refreshes the FP16 copy.          */
+dvnr_status dvnr_set_precision(dvnr_model m, int32_t precision, void* stream);
+
+/* Synchronous snapshot of the model state; reports DVNR_E_NONFINITE_INPUT
+ * if the last training volume held NaN/Inf (state still filled in).        */
+dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out);
+
+/* Train n models for cfg->steps iterations each (Sec. 3.2): per step and
+ * model, sample cfg->batch coordinates (uniform and boundary, Sec. 3.3),
+ * look up targets by trilinear interpolation of the model's volume after
+ * min/max normalisation (Sec. 3.1), run the encoding and MLP forward, the
+ * L1 (or L2) loss, the backward pass with the gradient scatter into the
+ * tables, and one Adam step. vol_dev[i] is model i's stored block
+ * ((hi-lo+2 ghost) voxels per axis). The value range is taken from the
+ * volume first (min/max over all stored voxels).
+ * FP16 precision: all n models run in one grouped kernel per step (they
+ * must share one encoding and MLP configuration), the steps are replayed
+ * from a CUDA graph. FP32 precision: the plain path, models one after
+ * another.
+ * final_loss_host: if not NULL, receives n mean losses of the last step
+ * and the call synchronises the stream.
+ * Errors: DVNR_E_INVALID, DVNR_E_UNSUPPORTED, DVNR_E_CUDA,
+ * DVNR_E_NONFINITE_INPUT (only when synchronising).                         */
+dvnr_status dvnr_train(dvnr_model* models, int32_t n,
+                       const float* const* vol_dev, const dvnr_train_cfg* cfg,
+                       void* stream, float* final_loss_host);
+
+/* One training step's forward and backward without the optimiser: the
+ * batch of iteration `iteration` (Philox counter), model slot 0, value range
+ * taken from vol_dev. Writes the requested outputs (see dvnr_step_outputs);
+ * the model's parameters and optimiser state are unchanged. Uses the same
+ * kernels as dvnr_train for cfg->precision (the FP16 path at loss scale
+ * 2^round(log2 batch)).                                                     */
+dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev,
+                            const dvnr_train_cfg* cfg, int64_t iteration,
+                            const dvnr_step_outputs* out, void* stream);
+
+/* Point inference (Sec. 3, Sec. 4.1): n points in global voxel coordinates
+ * (x, y, z float32 triples; voxel centre of global index j is at j) mapped
+ * into the model's unit domain, clamped to it, evaluated and de-normalised
+ * with the stored value range: out = y (vmax - vmin) + vmin.              */
+dvnr_status dvnr_decode_points(dvnr_model m, const float* xyz_dev, int64_t n,
+                               float* out_dev, void* stream);
+
+/* Decode to the grid (Sec. 3, Sec. 4.1): the owned voxels of the box,
+ * (hi-lo) per axis, x fastest, float32.                                     */
+dvnr_status dvnr_decode_grid(dvnr_model m, float* out_dev, void* stream);
+
+/* Direct volume rendering of n models (Sec. 4.3, reading stated in the
+ * project notes): each model is decoded to its owned grid, then one ray per
+ * pixel is marched orthographically along +z through the union of the owned
+ * boxes with spr samples at the centres of equal steps, trilinear on the
+ * grid of the block that owns the sample (clamped at that block's edge),
+ * transfer function `tf`, front-to-back compositing without early
+ * termination (sort-last order along +z). rgba_dev: h x w x 4 float32,
+ * premultiplied colour and opacity.                                         */
+dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf,
+                        int32_t w, int32_t h, int32_t spr, float* rgba_dev,
+                        void* stream);
+
+/* FP64 reduction of the reconstruction error between two float32 arrays
+ * (Sec. 5: PSNR from the mean squared error): out_host[0] = sum of squared
+ * differences, out_host[1] = max absolute difference. Synchronises.       */
+dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n,
+                             double* out_host, void* stream);
+
+/* Table indices of the 8 cell corners per level for n fixed-point
+ * coordinates (the indices the training and decoding kernels gather):
+ * idx_dev is n x n_levels x 8, corner k = (k&1, (k>>1)&1, (k>>2)&1).       */
+dvnr_status dvnr_corner_indices(dvnr_model m, const uint32_t* coords_dev,
+                                int64_t n, uint32_t* idx_dev, void* stream);
+
+/* Kernel timing for measurement: while enabled, every library kernel launch
+ * is bracketed by CUDA events recorded on the stream it is launched on, and
+ * the FP16 path launches its steps directly instead of replaying a CUDA
+ * graph. Off by default; enabling clears the accumulators.                */
+dvnr_status dvnr_profile_enable(int32_t on);
+
+/* Total device time (ms, sum over launches) and launch count of the kernels
+ * called `kernel` since profiling was enabled ("*" = every kernel).
+ * Synchronises the device. Unknown names report 0 launches.               */
+dvnr_status dvnr_profile_read(const char* kernel, double* total_ms, int64_t* launches);
+
+/* Number of kernels this library has launched since it was loaded; a CUDA
+ * graph replay adds the kernel nodes it runs.                              */
+int64_t dvnr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DVNR_H */

@@ -373,6 +373,8 @@ void orc_targets(const float* vol, int64_t nx, int64_t ny, int64_t nz,
  *   grad_mlp  += weight gradients (n_mlp), may be NULL
  *   y_out, dx0_out (n x in_dim, unscaled), margin_out: optional per sample;
  *             margin = min(|z| over hidden units, |y - t| for L1)
+ *   zabs_out  optional n x (H*width + 1): |z| of every hidden unit and, in
+ *             the last slot, |y - t| (L1) or +inf (L2)
  * Returns the mean loss.                                                    */
 typedef struct {
   double* h;   /* (H+1) x maxw activations, h[0] = x0 */
@@ -385,7 +387,7 @@ static double sample_fwd_bwd(const orc_cfg* c, const double* theta,
                              const uint32_t m[3], double target, int32_t loss,
                              int32_t mixed, double S, double inv_B,
                              const uint8_t* flip, double* gmlp, double* dx0,
-                             double* y_out, double* margin, scratch_t* s) {
+                             double* y_out, double* margin, double* zabs, scratch_t* s) {
   const int W = c->width, H = c->n_hidden, D = c->in_dim;
   const int maxw = W > D ? W : D;
   double* h = s->h;
@@ -405,6 +407,7 @@ static double sample_fwd_bwd(const orc_cfg* c, const double* theta,
       double r = acc > 0.0 ? acc : 0.0;
       HROW(k + 1)[j] = mixed ? orc_round_half(r) : r;
       if (fabs(acc) < mg) mg = fabs(acc);
+      if (zabs) zabs[k * W + j] = fabs(acc);
     }
   }
   const double* wout = theta + c->w_off[H];
@@ -417,9 +420,11 @@ static double sample_fwd_bwd(const orc_cfg* c, const double* theta,
     g = d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0);
     if (flip && flip[H * W]) g = (g == 0.0) ? 1.0 : -g;
     if (fabs(d) < mg) mg = fabs(d);
+    if (zabs) zabs[H * W] = fabs(d);
   } else {
     lval = d * d;
     g = 2.0 * d;
+    if (zabs) zabs[H * W] = INFINITY;
   }
   if (y_out) *y_out = y;
   if (margin) *margin = mg;
@@ -474,7 +479,8 @@ double orc_fwd_bwd(const orc_cfg* c, const double* theta, int64_t n,
                    const uint32_t* m, const double* target, int32_t loss,
                    int32_t mixed, double loss_scale, int64_t grad_norm_count,
                    const uint8_t* flip, double* grad_enc, double* grad_mlp,
-                   double* y_out, double* dx0_out, double* margin_out) {
+                   double* y_out, double* dx0_out, double* margin_out,
+                   double* zabs_out) {
   const int D = c->in_dim, W = c->width, H = c->n_hidden;
   const int maxw = W > D ? W : D;
   const int64_t nunits = (int64_t)H * W + 1;
@@ -505,7 +511,8 @@ double orc_fwd_bwd(const orc_cfg* c, const double* theta, int64_t n,
       loss_sum += sample_fwd_bwd(
           c, theta, m + 3 * i, target[i], loss, mixed, loss_scale, inv_B,
           flip ? flip + i * nunits : NULL, gmine, dx0_all + i * D,
-          y_out ? y_out + i : NULL, margin_out ? margin_out + i : NULL, &s);
+          y_out ? y_out + i : NULL, margin_out ? margin_out + i : NULL,
+          zabs_out ? zabs_out + i * nunits : NULL, &s);
     }
     free(s.h); free(s.z); free(s.dz); free(s.dh);
   }
@@ -599,7 +606,7 @@ double orc_train(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
     memset(grad, 0, sizeof(double) * (size_t)c->n_params);
     const double S = tc->mixed ? st->loss_scale : 1.0;
     last = orc_fwd_bwd(c, theta, B, m, tgt, tc->loss, tc->mixed, S, B, NULL,
-                       grad, grad + c->n_enc, NULL, NULL, NULL);
+                       grad, grad + c->n_enc, NULL, NULL, NULL, NULL);
     if (loss_hist) loss_hist[s] = last;
     orc_adam(c, tc, st, theta, mom1, mom2, grad);
     st->iter += 1;

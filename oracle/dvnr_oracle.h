@@ -102,7 +102,8 @@ double orc_fwd_bwd(const orc_cfg* c, const double* theta, int64_t n,
                    const uint32_t* m, const double* target, int32_t loss,
                    int32_t mixed, double loss_scale, int64_t grad_norm_count,
                    const uint8_t* flip, double* grad_enc, double* grad_mlp,
-                   double* y_out, double* dx0_out, double* margin_out);
+                   double* y_out, double* dx0_out, double* margin_out,
+                   double* zabs_out);
 
 void orc_adam(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
               double* theta, double* mom1, double* mom2, const double* grad);

@@ -99,7 +99,8 @@ def _lib_handle():
             lib.orc_targets.argtypes = [_P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, _P,
                                         C.c_double, C.c_double, _P]
             lib.orc_fwd_bwd.argtypes = [C.POINTER(_Cfg), _P, C.c_int64, _P, _P, C.c_int32,
-                                        C.c_int32, C.c_double, C.c_int64, _P, _P, _P, _P, _P, _P]
+                                        C.c_int32, C.c_double, C.c_int64, _P, _P, _P, _P, _P, _P,
+                                        _P]
             lib.orc_fwd_bwd.restype = C.c_double
             lib.orc_adam.argtypes = [C.POINTER(_Cfg), C.POINTER(_TrainCfg), C.POINTER(_State),
                                      _P, _P, _P, _P]
@@ -220,9 +221,9 @@ def encode(cfg: Config, theta, m, mixed=False):
 
 
 def fwd_bwd(cfg: Config, theta, m, target, loss=0, mixed=False, loss_scale=1.0,
-            grad_norm_count=None, flip=None, want_grads=True):
+            grad_norm_count=None, flip=None, want_grads=True, want_zabs=False):
     """Forward + backward of one batch. Returns a dict with loss, grad_enc,
-    grad_mlp, y, dx0, margin (see the C header)."""
+    grad_mlp, y, dx0, margin and optionally zabs (see the C header)."""
     th = _arr(theta, np.float64)
     mm = _arr(m, np.uint32).reshape(-1, 3)
     n = mm.shape[0]
@@ -233,10 +234,12 @@ def fwd_bwd(cfg: Config, theta, m, target, loss=0, mixed=False, loss_scale=1.0,
     dx0 = np.zeros((n, cfg.in_dim), dtype=np.float64)
     margin = np.zeros(n, dtype=np.float64)
     fl = None if flip is None else _arr(flip, np.uint8)
+    zabs = np.zeros((n, cfg.n_hidden * cfg.width + 1)) if want_zabs else None
     lval = _lib_handle().orc_fwd_bwd(
         cfg.ref, _ptr(th), n, _ptr(mm), _ptr(t), int(loss), int(mixed), float(loss_scale),
-        int(grad_norm_count or n), _ptr(fl), _ptr(ge), _ptr(gm), _ptr(y), _ptr(dx0), _ptr(margin))
-    return dict(loss=lval, grad_enc=ge, grad_mlp=gm, y=y, dx0=dx0, margin=margin)
+        int(grad_norm_count or n), _ptr(fl), _ptr(ge), _ptr(gm), _ptr(y), _ptr(dx0), _ptr(margin),
+        _ptr(zabs))
+    return dict(loss=lval, grad_enc=ge, grad_mlp=gm, y=y, dx0=dx0, margin=margin, zabs=zabs)
 
 
 class TrainConfig:

@@ -1,0 +1,596 @@
+// api.cu -- host implementation of the libdvnr C ABI (include/dvnr.h).
+//
+// Model lifecycle, argument checks, the per-step orchestration of the plain
+// FP32 path and of the grouped FP16 tensor-core path (CUDA-graph replay),
+// decoding and rendering. Every call returns a status and never aborts.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "dvnr_internal.cuh"
+#include "mp_path.cuh"
+
+namespace dvnr {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+dvnr_status cuda_status(cudaError_t e, const char* what) {
+  set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? DVNR_E_OOM : DVNR_E_CUDA;
+}
+
+namespace {
+
+dvnr_status fail(dvnr_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+// Half-normal quantile table in 24-bit fixed point (Sec. 3.3 boundary
+// samples): knot k < 4096 at p = k/4096, the last knot at p = 1 - 2^-24,
+// q(p) = sigma sqrt(2) erfinv(p); erfinv by safeguarded Newton steps on erf.
+double erfinv_newton(double p) {
+  if (p <= 0.0) return 0.0;
+  double lo = 0.0, hi = 8.0, x = 1.0;
+  for (int it = 0; it < 200; ++it) {
+    const double f = std::erf(x) - p;
+    if (f < 0.0) lo = x; else hi = x;
+    const double d = 1.1283791670955126 * std::exp(-x * x);
+    double xn = x - f / d;
+    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+    if (xn == x || hi - lo <= 0.0) break;
+    x = xn;
+  }
+  return x;
+}
+
+void quantile_table(float sigma_f, std::vector<int32_t>& tab) {
+  const double sigma = (double)sigma_f;
+  tab.resize(kQTab + 1);
+  for (int k = 0; k <= kQTab; ++k) {
+    const double p = (k < kQTab) ? (double)k / kQTab : 1.0 - std::ldexp(1.0, -24);
+    const double x = (k == 0) ? 0.0 : erfinv_newton(p);
+    const double q = sigma * (1.41421356237309504880 * x);
+    tab[k] = (int32_t)std::llround(q * 16777216.0);
+  }
+}
+
+dvnr_status check_enc_mlp(const dvnr_enc_cfg* enc, const dvnr_mlp_cfg* mlp) {
+  if (!enc || !mlp) return fail(DVNR_E_INVALID, "NULL configuration");
+  if (enc->n_levels < 1 || enc->n_levels > kMaxLevels)
+    return fail(DVNR_E_INVALID, "n_levels must be in [1, %d]", kMaxLevels);
+  const int F = enc->n_features;
+  if (!(F == 1 || F == 2 || F == 4 || F == 8))
+    return fail(DVNR_E_INVALID, "n_features must be 1, 2, 4 or 8");
+  if (enc->log2_T < 4 || enc->log2_T > 24) return fail(DVNR_E_INVALID, "log2_T must be in [4, 24]");
+  if (enc->base_res < 1 || !(enc->growth >= 1.0) || !std::isfinite(enc->growth))
+    return fail(DVNR_E_INVALID, "base_res >= 1 and finite growth >= 1 required");
+  if (!(mlp->width == 16 || mlp->width == 32 || mlp->width == 64))
+    return fail(DVNR_E_UNSUPPORTED, "width must be 16, 32 or 64");
+  if (mlp->n_hidden < 1 || mlp->n_hidden > kMaxHidden)
+    return fail(DVNR_E_INVALID, "n_hidden must be in [1, %d]", kMaxHidden);
+  if (enc->n_levels * F > 256) return fail(DVNR_E_UNSUPPORTED, "n_levels * n_features > 256");
+  return DVNR_OK;
+}
+
+bool same_arch(const dvnr_model a, const dvnr_model b) {
+  return a->enc.n_levels == b->enc.n_levels && a->enc.n_features == b->enc.n_features &&
+         a->enc.log2_T == b->enc.log2_T && a->enc.base_res == b->enc.base_res &&
+         a->enc.growth == b->enc.growth && a->mlp.width == b->mlp.width &&
+         a->mlp.n_hidden == b->mlp.n_hidden;
+}
+
+dvnr_status check_train_cfg(const dvnr_train_cfg* c) {
+  if (!c) return fail(DVNR_E_INVALID, "NULL train configuration");
+  if (c->batch < 1) return fail(DVNR_E_INVALID, "batch must be >= 1");
+  if (c->steps < 0) return fail(DVNR_E_INVALID, "steps must be >= 0");
+  if (!(c->lr > 0.f) || !(c->beta1 >= 0.f && c->beta1 < 1.f) || !(c->beta2 >= 0.f && c->beta2 < 1.f) ||
+      !(c->eps >= 0.f) || !(c->weight_decay >= 0.f))
+    return fail(DVNR_E_INVALID, "Adam hyper-parameters out of range");
+  if (!(c->lambda_bnd >= 0.f && c->lambda_bnd <= 1.f))
+    return fail(DVNR_E_INVALID, "lambda_bnd must be in [0, 1]");
+  if (c->lambda_bnd > 0.f && !(c->sigma_bnd > 0.f && c->sigma_bnd <= 1.f))
+    return fail(DVNR_E_INVALID, "sigma_bnd must be in (0, 1]");
+  if (c->precision != DVNR_FP32 && c->precision != DVNR_FP16)
+    return fail(DVNR_E_INVALID, "precision must be DVNR_FP32 or DVNR_FP16");
+  if (c->loss != DVNR_LOSS_L1 && c->loss != DVNR_LOSS_L2)
+    return fail(DVNR_E_INVALID, "loss must be DVNR_LOSS_L1 or DVNR_LOSS_L2");
+  if (c->precision == DVNR_FP16 && c->growth_interval < 1)
+    return fail(DVNR_E_INVALID, "growth_interval must be >= 1");
+  return DVNR_OK;
+}
+
+dvnr_status use_device(dvnr_model m) {
+  int cur = -1;
+  DVNR_CUDA(cudaGetDevice(&cur));
+  if (cur != m->device) DVNR_CUDA(cudaSetDevice(m->device));
+  return DVNR_OK;
+}
+
+int64_t stored_voxels(const dvnr_model m) { return m->dims[0] * m->dims[1] * m->dims[2]; }
+
+float initial_loss_scale(int32_t batch) {
+  // 2^round(log2 B): the scaled L1 output gradient S/B is then ~1
+  return std::ldexp(1.0f, (int)std::lround(std::log2((double)batch)));
+}
+
+dvnr_status prepare_qtab(dvnr_model m, float sigma, cudaStream_t s) {
+  if (m->qtab_sigma == sigma) return DVNR_OK;
+  std::vector<int32_t> tab;
+  quantile_table(sigma > 0.f ? sigma : 0.005f, tab);
+  DVNR_CUDA(cudaMemcpyAsync(m->qtab, tab.data(), tab.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+  DVNR_CUDA(cudaStreamSynchronize(s));  // the host table is released below
+  m->qtab_sigma = sigma;
+  return DVNR_OK;
+}
+
+SampleParams sample_params(dvnr_model m, const dvnr_train_cfg* cfg, uint32_t slot) {
+  SampleParams sp;
+  sp.key = make_uint2((uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32));
+  sp.model = slot;
+  sp.n_bnd = (int32_t)std::floor((double)cfg->lambda_bnd * (double)cfg->batch);
+  sp.qtab = m->qtab;
+  return sp;
+}
+
+AdamHyper adam_hyper(const dvnr_train_cfg* cfg, bool mixed) {
+  AdamHyper h;
+  h.lr = cfg->lr;
+  h.beta1 = cfg->beta1;
+  h.beta2 = cfg->beta2;
+  h.eps = cfg->eps;
+  h.weight_decay = cfg->weight_decay;
+  h.inv_batch = 1.0f / (float)cfg->batch;
+  h.mixed = mixed ? 1 : 0;
+  h.growth_interval = cfg->growth_interval > 0 ? cfg->growth_interval : (1 << 30);
+  return h;
+}
+
+// Per-model AdamModelPtrs live at the end of the model block.
+AdamModelPtrs* adam_ptrs_dev(dvnr_model m) {
+  return reinterpret_cast<AdamModelPtrs*>(reinterpret_cast<char*>(m->qtab) +
+                                          align256((kQTab + 1) * sizeof(int32_t)));
+}
+
+}  // namespace
+}  // namespace dvnr
+
+using namespace dvnr;
+
+extern "C" {
+
+int32_t dvnr_abi_version(void) { return DVNR_ABI_VERSION; }
+
+const char* dvnr_last_error(void) { return g_err; }
+
+dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr_mlp_cfg* mlp,
+                        uint64_t seed, dvnr_model* out) {
+  g_err[0] = 0;
+  if (!out) return fail(DVNR_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!box) return fail(DVNR_E_INVALID, "box is NULL");
+  dvnr_status rc = check_enc_mlp(enc, mlp);
+  if (rc != DVNR_OK) return rc;
+  if (box->ghost < 0) return fail(DVNR_E_INVALID, "ghost must be >= 0");
+  int64_t dims[3];
+  for (int a = 0; a < 3; ++a) {
+    if (box->hi[a] <= box->lo[a]) return fail(DVNR_E_INVALID, "box must have hi > lo on every axis");
+    dims[a] = box->hi[a] - box->lo[a] + 2 * (int64_t)box->ghost;
+    if (dims[a] < 2) return fail(DVNR_E_INVALID, "stored block needs >= 2 voxels per axis");
+    if (dims[a] > (1 << 20)) return fail(DVNR_E_INVALID, "block too large");
+  }
+  dvnr_model m = new (std::nothrow) dvnr_model_s();
+  if (!m) return fail(DVNR_E_OOM, "host allocation failed");
+  m->box = *box;
+  m->enc = *enc;
+  m->mlp = *mlp;
+  for (int a = 0; a < 3; ++a) m->dims[a] = dims[a];
+  cudaError_t ce = cudaGetDevice(&m->device);
+  if (ce != cudaSuccess) {
+    delete m;
+    return cuda_status(ce, "cudaGetDevice");
+  }
+  // Level layout: N_l = floor(base growth^l); dense iff (N_l + 1)^3 <= T.
+  LevelTab& lv = m->lv;
+  lv.L = enc->n_levels;
+  lv.F = enc->n_features;
+  lv.in_dim = enc->n_levels * enc->n_features;
+  const int64_t T = 1LL << enc->log2_T;
+  lv.hash_mask = (uint32_t)(T - 1);
+  lv.dense_mask = 0;
+  int64_t off = 0;
+  for (int l = 0; l < lv.L; ++l) {
+    const double r = std::floor((double)enc->base_res * std::pow(enc->growth, (double)l));
+    if (r > (double)(1 << 21)) {
+      delete m;
+      return fail(DVNR_E_INVALID, "level %d resolution exceeds 2^21", l);
+    }
+    const int64_t N = (int64_t)r;
+    lv.N[l] = (uint32_t)N;
+    const int64_t verts = (N + 1) * (N + 1) * (N + 1);
+    const bool dense = verts <= T;
+    if (dense) lv.dense_mask |= 1u << l;
+    lv.off[l] = off;
+    off += (dense ? verts : T) * lv.F;
+  }
+  m->n_enc = off;
+  int64_t w = off;
+  const int W = mlp->width, H = mlp->n_hidden;
+  for (int k = 0; k < H; ++k) {
+    const int fan_in = k == 0 ? lv.in_dim : W;
+    m->w_off[k] = w;
+    m->glorot[k] = std::sqrt(6.0 / (double)(fan_in + W));
+    w += (int64_t)W * fan_in;
+  }
+  m->w_off[H] = w;
+  m->glorot[H] = std::sqrt(6.0 / (double)(W + 1));
+  w += W;
+  m->n_params = w;
+  m->n_mlp = w - m->n_enc;
+  if (m->n_params >= (1LL << 31)) {
+    delete m;
+    return fail(DVNR_E_UNSUPPORTED, "more than 2^31 parameters");
+  }
+  const size_t P = (size_t)m->n_params;
+  const size_t b32 = align256(P * 4), b16 = align256(P * 2), bst = align256(sizeof(ModelState)),
+               bq = align256((kQTab + 1) * sizeof(int32_t)), bap = align256(sizeof(AdamModelPtrs));
+  ce = cudaMalloc(&m->block, 4 * b32 + b16 + bst + bq + bap);
+  if (ce != cudaSuccess) {
+    delete m;
+    return cuda_status(ce, "cudaMalloc(model)");
+  }
+  char* p = static_cast<char*>(m->block);
+  m->theta = reinterpret_cast<float*>(p); p += b32;
+  m->m1 = reinterpret_cast<float*>(p); p += b32;
+  m->m2 = reinterpret_cast<float*>(p); p += b32;
+  m->grad = reinterpret_cast<float*>(p); p += b32;
+  m->theta16 = reinterpret_cast<__half*>(p); p += b16;
+  m->st = reinterpret_cast<ModelState*>(p); p += bst;
+  m->qtab = reinterpret_cast<int32_t*>(p); p += bq;
+  AdamModelPtrs ap{m->theta, m->m1, m->m2, m->grad, m->theta16, m->st};
+  ModelState st0{};
+  st0.enc_min = float_to_ordered(0.f);
+  st0.enc_max = float_to_ordered(1.f);
+  st0.loss_scale = 1.f;
+  auto cleanup = [&](dvnr_status s) {
+    cudaFree(m->block);
+    delete m;
+    return s;
+  };
+  if ((rc = launch_init_params(m, seed, 0)) != DVNR_OK) return cleanup(rc);
+  if ((ce = cudaMemset(m->m1, 0, 3 * b32)) != cudaSuccess) return cleanup(cuda_status(ce, "cudaMemset"));
+  if ((ce = cudaMemcpy(m->st, &st0, sizeof(st0), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaMemcpy(adam_ptrs_dev(m), &ap, sizeof(ap), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (ce = cudaDeviceSynchronize()) != cudaSuccess)
+    return cleanup(cuda_status(ce, "dvnr_create"));
+  *out = m;
+  return DVNR_OK;
+}
+
+void dvnr_destroy(dvnr_model m) {
+  if (!m) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(m->device);
+  cudaDeviceSynchronize();
+  mp_release(m);
+  if (m->ws.base) cudaFree(m->ws.base);
+  if (m->grid_ws) cudaFree(m->grid_ws);
+  cudaFree(m->block);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete m;
+}
+
+dvnr_status dvnr_param_count(dvnr_model m, int64_t* n_enc, int64_t* n_mlp) {
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (n_enc) *n_enc = m->n_enc;
+  if (n_mlp) *n_mlp = m->n_mlp;
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_get_weights(dvnr_model m, float* host, int64_t n) {
+  if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
+  if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  DVNR_CUDA(cudaMemcpy(host, m->theta, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_set_weights(dvnr_model m, const float* host, int64_t n) {
+  if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
+  if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  DVNR_CUDA(cudaMemcpy(m->theta, host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  if ((rc = launch_refresh_half(m, 0)) != DVNR_OK) return rc;
+  DVNR_CUDA(cudaMemset(m->m1, 0, (size_t)n * 4));
+  DVNR_CUDA(cudaMemset(m->m2, 0, (size_t)n * 4));
+  DVNR_CUDA(cudaMemset(m->grad, 0, (size_t)n * 4));
+  if ((rc = launch_state_reset(m->st, 1.f, 0)) != DVNR_OK) return rc;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_copy_weights(dvnr_model dst, dvnr_model src, void* stream) {
+  if (!dst || !src) return fail(DVNR_E_INVALID, "NULL model");
+  if (!same_arch(dst, src)) return fail(DVNR_E_INVALID, "models differ in encoding or MLP configuration");
+  if (dst->device != src->device) return fail(DVNR_E_INVALID, "models live on different devices");
+  if (dst == src) return DVNR_OK;
+  dvnr_status rc = use_device(dst);
+  if (rc != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t n = (size_t)dst->n_params;
+  DVNR_CUDA(cudaMemcpyAsync(dst->theta, src->theta, n * 4, cudaMemcpyDeviceToDevice, s));
+  DVNR_CUDA(cudaMemcpyAsync(dst->theta16, src->theta16, n * 2, cudaMemcpyDeviceToDevice, s));
+  DVNR_CUDA(cudaMemcpyAsync(dst->st, src->st, 2 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  DVNR_CUDA(cudaMemsetAsync(dst->m1, 0, n * 4, s));
+  DVNR_CUDA(cudaMemsetAsync(dst->m2, 0, n * 4, s));
+  DVNR_CUDA(cudaMemsetAsync(dst->grad, 0, n * 4, s));
+  if ((rc = launch_state_reset(dst->st, 1.f, s)) != DVNR_OK) return rc;
+  dst->precision = src->precision;
+  dst->scale_initialized = false;
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_set_precision(dvnr_model m, int32_t precision, void* stream) {
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (precision != DVNR_FP32 && precision != DVNR_FP16) return fail(DVNR_E_INVALID, "bad precision");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  if (precision == DVNR_FP16 && m->precision != DVNR_FP16) {
+    if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+    if ((rc = launch_refresh_half(m, (cudaStream_t)stream)) != DVNR_OK) return rc;
+  }
+  m->precision = precision;
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out) {
+  if (!m || !out) return fail(DVNR_E_INVALID, "NULL argument");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  ModelState st;
+  DVNR_CUDA(cudaMemcpy(&st, m->st, sizeof(st), cudaMemcpyDeviceToHost));
+  out->vmin = ordered_to_float(st.enc_min);
+  out->vmax = ordered_to_float(st.enc_max);
+  out->loss_scale = st.loss_scale;
+  out->last_loss = st.last_loss;
+  out->iter = st.iter;
+  out->adam_t = st.adam_t;
+  out->skipped = st.skipped;
+  out->n_enc = m->n_enc;
+  out->n_mlp = m->n_mlp;
+  out->precision = m->precision;
+  out->nonfinite_input = st.nonfinite ? 1 : 0;
+  if (st.timeouts) return fail(DVNR_E_TIMEOUT, "a bounded device wait gave up (%u)", st.timeouts);
+  if (st.nonfinite) return fail(DVNR_E_NONFINITE_INPUT, "the last training volume held NaN/Inf");
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_dev,
+                       const dvnr_train_cfg* cfg, void* stream, float* final_loss_host) {
+  g_err[0] = 0;
+  if (n < 1 || !models || !vol_dev) return fail(DVNR_E_INVALID, "need n >= 1 models and volumes");
+  dvnr_status rc = check_train_cfg(cfg);
+  if (rc != DVNR_OK) return rc;
+  for (int i = 0; i < n; ++i) {
+    if (!models[i] || !vol_dev[i]) return fail(DVNR_E_INVALID, "model or volume %d is NULL", i);
+    if (models[i]->device != models[0]->device) return fail(DVNR_E_INVALID, "models on different devices");
+    for (int j = 0; j < i; ++j)
+      if (models[j] == models[i]) return fail(DVNR_E_INVALID, "model %d appears twice", i);
+  }
+  const bool mixed = cfg->precision == DVNR_FP16;
+  if (mixed) {
+    for (int i = 0; i < n; ++i) {
+      if (!same_arch(models[i], models[0]))
+        return fail(DVNR_E_INVALID, "grouped FP16 training needs one configuration for all models");
+      if (!mp_supported(models[i]))
+        return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+    }
+  }
+  if ((rc = use_device(models[0])) != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n; ++i) {
+    dvnr_model m = models[i];
+    if (cfg->lambda_bnd > 0.f && (rc = prepare_qtab(m, cfg->sigma_bnd, s)) != DVNR_OK) return rc;
+    if ((rc = launch_minmax(vol_dev[i], stored_voxels(m), m->st, s)) != DVNR_OK) return rc;
+    m->precision = cfg->precision;
+    if (mixed && !m->scale_initialized) {
+      if ((rc = launch_state_reset_scale(m->st, initial_loss_scale(cfg->batch), s)) != DVNR_OK) return rc;
+      m->scale_initialized = true;
+    }
+  }
+  const AdamHyper h = adam_hyper(cfg, mixed);
+  if (mixed) {
+    rc = mp_train(models, n, vol_dev, cfg, h, s);
+    if (rc != DVNR_OK) return rc;
+  } else {
+    for (int i = 0; i < n; ++i) {
+      dvnr_model m = models[i];
+      if ((rc = fp32_ensure_workspace(m, cfg->batch)) != DVNR_OK) return rc;
+      Fp32StepArgs a{};
+      a.m = m;
+      a.vol = vol_dev[i];
+      a.sp = sample_params(m, cfg, (uint32_t)i);
+      a.batch = cfg->batch;
+      a.loss = cfg->loss;
+      a.explicit_iter = false;
+      for (int64_t step = 0; step < cfg->steps; ++step) {
+        if ((rc = fp32_forward_backward(a, s)) != DVNR_OK) return rc;
+        if ((rc = launch_adam(adam_ptrs_dev(m), 1, m->n_params, h, s)) != DVNR_OK) return rc;
+      }
+    }
+  }
+  if (final_loss_host) {
+    DVNR_CUDA(cudaStreamSynchronize(s));
+    bool bad = false;
+    for (int i = 0; i < n; ++i) {
+      ModelState st;
+      DVNR_CUDA(cudaMemcpy(&st, models[i]->st, sizeof(st), cudaMemcpyDeviceToHost));
+      final_loss_host[i] = st.last_loss;
+      bad |= st.nonfinite != 0;
+      if (st.timeouts) return fail(DVNR_E_TIMEOUT, "a bounded device wait gave up in model %d", i);
+    }
+    if (bad) return fail(DVNR_E_NONFINITE_INPUT, "a training volume held NaN/Inf");
+  }
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev, const dvnr_train_cfg* cfg,
+                            int64_t iteration, const dvnr_step_outputs* out, void* stream) {
+  g_err[0] = 0;
+  if (!m || !vol_dev) return fail(DVNR_E_INVALID, "NULL model or volume");
+  dvnr_status rc = check_train_cfg(cfg);
+  if (rc != DVNR_OK) return rc;
+  if (iteration < 0) return fail(DVNR_E_INVALID, "iteration must be >= 0");
+  const bool mixed = cfg->precision == DVNR_FP16;
+  if (mixed && !mp_supported(m))
+    return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+  if ((rc = use_device(m)) != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  dvnr_step_outputs o{};
+  if (out) o = *out;
+  if (cfg->lambda_bnd > 0.f && (rc = prepare_qtab(m, cfg->sigma_bnd, s)) != DVNR_OK) return rc;
+  if ((rc = launch_minmax(vol_dev, stored_voxels(m), m->st, s)) != DVNR_OK) return rc;
+  DVNR_CUDA(cudaMemsetAsync(&m->st->loss_sum, 0, sizeof(float), s));
+  float S = 1.f;
+  if (mixed) {
+    S = initial_loss_scale(cfg->batch);
+    MpStepDebug dbg{o.y, o.dx0, o.target, o.coords};
+    rc = mp_train_grad(m, vol_dev, cfg, (uint32_t)iteration, S, dbg, s);
+  } else {
+    Fp32StepArgs a{};
+    a.m = m;
+    a.vol = vol_dev;
+    a.sp = sample_params(m, cfg, 0);
+    a.batch = cfg->batch;
+    a.loss = cfg->loss;
+    a.explicit_iter = true;
+    a.iter = (uint32_t)iteration;
+    a.y_out = o.y;
+    a.dx0_out = o.dx0;
+    a.tgt_out = o.target;
+    a.coords_out = o.coords;
+    rc = fp32_forward_backward(a, s);
+  }
+  if (rc != DVNR_OK) return rc;
+  return launch_finish_grad(m, S, 1.0f / (float)cfg->batch, o.grad, o.loss, s);
+}
+
+dvnr_status dvnr_decode_points(dvnr_model m, const float* xyz_dev, int64_t n, float* out_dev,
+                               void* stream) {
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (n < 0) return fail(DVNR_E_INVALID, "n must be >= 0");
+  if (n == 0) return DVNR_OK;
+  if (!xyz_dev || !out_dev) return fail(DVNR_E_INVALID, "NULL buffer");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  if (m->precision == DVNR_FP16) return mp_decode(m, xyz_dev, n, 0, out_dev, (cudaStream_t)stream);
+  return fp32_decode_unit(m, nullptr, xyz_dev, n, 0, out_dev, (cudaStream_t)stream);
+}
+
+dvnr_status dvnr_decode_grid(dvnr_model m, float* out_dev, void* stream) {
+  if (!m || !out_dev) return fail(DVNR_E_INVALID, "NULL argument");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  const int64_t n = (m->box.hi[0] - m->box.lo[0]) * (m->box.hi[1] - m->box.lo[1]) *
+                    (m->box.hi[2] - m->box.lo[2]);
+  if (m->precision == DVNR_FP16) return mp_decode(m, nullptr, n, 1, out_dev, (cudaStream_t)stream);
+  return fp32_decode_unit(m, nullptr, nullptr, n, 1, out_dev, (cudaStream_t)stream);
+}
+
+dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w, int32_t h,
+                        int32_t spr, float* rgba_dev, void* stream) {
+  g_err[0] = 0;
+  if (n < 1 || !models || !tf || !rgba_dev) return fail(DVNR_E_INVALID, "NULL argument or n < 1");
+  if (w < 1 || h < 1 || spr < 1) return fail(DVNR_E_INVALID, "w, h, spr must be >= 1");
+  for (int i = 0; i < n; ++i)
+    if (!models[i]) return fail(DVNR_E_INVALID, "model %d is NULL", i);
+  dvnr_status rc = use_device(models[0]);
+  if (rc != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<RenderBlock> blocks((size_t)n);
+  float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
+  for (int i = 0; i < n; ++i) {
+    dvnr_model m = models[i];
+    const size_t ne = (size_t)((m->box.hi[0] - m->box.lo[0]) * (m->box.hi[1] - m->box.lo[1]) *
+                               (m->box.hi[2] - m->box.lo[2]));
+    if (m->grid_ws_elems < ne) {
+      if (m->grid_ws) {
+        DVNR_CUDA(cudaStreamSynchronize(s));
+        cudaFree(m->grid_ws);
+        m->grid_ws = nullptr;
+        m->grid_ws_elems = 0;
+      }
+      DVNR_CUDA(cudaMalloc(&m->grid_ws, ne * sizeof(float)));
+      m->grid_ws_elems = ne;
+    }
+    if ((rc = dvnr_decode_grid(m, m->grid_ws, stream)) != DVNR_OK) return rc;
+    RenderBlock& b = blocks[(size_t)i];
+    for (int a = 0; a < 3; ++a) {
+      b.lo[a] = (float)m->box.lo[a];
+      b.hi[a] = (float)m->box.hi[a];
+      b.e[a] = (int32_t)(m->box.hi[a] - m->box.lo[a]);
+      lo[a] = std::min(lo[a], b.lo[a]);
+      hi[a] = std::max(hi[a], b.hi[a]);
+    }
+    b.pad = 0;
+    b.grid = m->grid_ws;
+  }
+  std::stable_sort(blocks.begin(), blocks.end(),
+                   [](const RenderBlock& a, const RenderBlock& b) { return a.lo[2] < b.lo[2]; });
+  RenderBlock* dblocks = nullptr;
+  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dblocks), blocks.size() * sizeof(RenderBlock), s));
+  DVNR_CUDA(cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(RenderBlock),
+                            cudaMemcpyHostToDevice, s));
+  rc = launch_render(dblocks, n, lo, hi, *tf, w, h, spr, rgba_dev, s);
+  cudaFreeAsync(dblocks, s);
+  if (rc == DVNR_OK) DVNR_CUDA(cudaStreamSynchronize(s));  // the host block table is released
+  return rc;
+}
+
+dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n, double* out_host,
+                             void* stream) {
+  if (!out_host || n < 0 || (n > 0 && (!a_dev || !b_dev))) return fail(DVNR_E_INVALID, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* d = nullptr;
+  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), 2 * sizeof(double), s));
+  dvnr_status rc = launch_error_stats(a_dev, b_dev, n, d, s);
+  if (rc == DVNR_OK) {
+    cudaError_t e = cudaMemcpyAsync(out_host, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_status(e, "dvnr_error_stats");
+  }
+  cudaFreeAsync(d, s);
+  return rc;
+}
+
+dvnr_status dvnr_corner_indices(dvnr_model m, const uint32_t* coords_dev, int64_t n, uint32_t* idx_dev,
+                                void* stream) {
+  if (!m || n < 0 || (n > 0 && (!coords_dev || !idx_dev))) return fail(DVNR_E_INVALID, "bad argument");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  return launch_corner_indices(m, coords_dev, n, idx_dev, (cudaStream_t)stream);
+}
+
+}  // extern "C"

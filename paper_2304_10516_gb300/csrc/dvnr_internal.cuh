@@ -1,0 +1,296 @@
+// dvnr_internal.cuh -- shared declarations of the libdvnr translation units.
+//
+// Device helpers for the DVNR hot path (arXiv 2304.10516): counter-based
+// sampling, 24-bit fixed-point lattice positions, the hash-grid corner index
+// (Sec. 3, after Mueller et al. 2022), the model's device state, and the
+// kernel launchers implemented in the other .cu files.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+
+#include "../../include/dvnr.h"
+
+namespace dvnr {
+
+constexpr int kMaxLevels = 32;
+constexpr int kMaxHidden = 8;
+constexpr int kQTab = 4096;          // segments of the half-normal quantile table
+constexpr uint32_t kFixOne = 1u << 24;  // unit coordinate u = m / 2^24
+constexpr uint32_t kPurposeInit = 0x494E4954u;    // 'INIT'
+constexpr uint32_t kPurposeSample = 0x53414D00u;  // 'SAM\0' + redraw attempt
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const char* fmt, ...);
+dvnr_status cuda_status(cudaError_t e, const char* what);
+#define DVNR_CUDA(call)                                           \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return ::dvnr::cuda_status(e_, #call); \
+  } while (0)
+
+// ------------------------------------------------------------- profiling ----
+// RAII bracket of one kernel launch: counts it and, while profiling is on,
+// records CUDA events around it on its stream.
+struct ProfScope {
+  ProfScope(const char* name, cudaStream_t s);
+  ~ProfScope();
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+bool profiling_on();
+void count_launches(int64_t n);
+
+// ----------------------------------------------------------- level table ----
+// Per-level layout of the hash-grid tables (kernel parameter, by value).
+struct LevelTab {
+  int32_t L, F, in_dim;
+  uint32_t hash_mask;              // T - 1
+  uint32_t dense_mask;             // bit l: level l stored densely
+  uint32_t N[kMaxLevels];          // resolution N_l
+  int64_t off[kMaxLevels];         // first parameter of level l
+};
+
+// ------------------------------------------------------- device state ------
+// Per-model state that lives on the device so that whole training steps can
+// be captured in a CUDA graph and replayed.
+struct ModelState {
+  uint32_t enc_min, enc_max;  // order-preserving encodings of the value range
+  uint32_t nonfinite;         // training volume held NaN/Inf
+  uint32_t overflow;          // a non-finite gradient was produced this step
+  float loss_scale;           // dynamic loss scale S (FP16 path)
+  uint32_t good_steps;        // finite steps since the last scale change
+  uint32_t iter;              // iterations drawn (Philox counter word 1)
+  uint32_t adam_t;            // Adam steps applied
+  uint32_t skipped;           // steps skipped for non-finite gradients
+  uint32_t done_blocks;       // Adam last-block counter
+  float loss_sum;             // sum of per-sample losses of this step
+  float last_loss;            // mean loss of the last completed step
+  uint32_t timeouts;          // bounded device waits that gave up
+  uint32_t pad[3];
+};
+
+__host__ __device__ inline uint32_t float_to_ordered(float f) {
+#ifdef __CUDA_ARCH__
+  uint32_t b = __float_as_uint(f);
+#else
+  uint32_t b;
+  memcpy(&b, &f, 4);
+#endif
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__host__ __device__ inline float ordered_to_float(uint32_t e) {
+  uint32_t b = (e & 0x80000000u) ? (e & 0x7FFFFFFFu) : ~e;
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float f;
+  memcpy(&f, &b, 4);
+  return f;
+#endif
+}
+
+// ------------------------------------------------------------ the model ----
+struct Fp32Workspace {
+  int64_t batch = 0;
+  float* x0 = nullptr;     // batch x in_dim
+  float* act = nullptr;    // n_hidden x batch x width  (H_1 .. H_H)
+  float* dz = nullptr;     // 2 x batch x width (ping-pong)
+  float* dx0 = nullptr;    // batch x in_dim
+  float* tgt = nullptr;    // batch
+  uint32_t* coords = nullptr;  // batch x 3
+  void* base = nullptr;
+};
+
+}  // namespace dvnr
+
+struct dvnr_model_s {
+  int device = 0;
+  dvnr_box box{};
+  dvnr_enc_cfg enc{};
+  dvnr_mlp_cfg mlp{};
+  dvnr::LevelTab lv{};
+  int64_t dims[3] = {0, 0, 0};  // stored voxels per axis (ghost included)
+  int64_t n_enc = 0, n_mlp = 0, n_params = 0;
+  int64_t w_off[dvnr::kMaxHidden + 1] = {};
+  double glorot[dvnr::kMaxHidden + 1] = {};  // init limit of each matrix
+  // parameter block: theta | m1 | m2 | grad (fp32), theta16, state, qtab
+  void* block = nullptr;
+  float* theta = nullptr;
+  float* m1 = nullptr;
+  float* m2 = nullptr;
+  float* grad = nullptr;
+  __half* theta16 = nullptr;
+  dvnr::ModelState* st = nullptr;
+  int32_t* qtab = nullptr;
+  float qtab_sigma = -1.f;
+  int32_t precision = DVNR_FP32;
+  bool scale_initialized = false;  // FP16 loss scale set for this model
+  dvnr::Fp32Workspace ws;
+  void* mp = nullptr;              // FP16 path resources (mp_path.cu)
+  float* grid_ws = nullptr;  // decoded grid for rendering
+  size_t grid_ws_elems = 0;
+};
+
+namespace dvnr {
+
+// ------------------------------------------------------- device helpers ----
+#ifdef __CUDACC__
+// Philox-4x32-10 (Salmon et al. 2011), ten rounds with bumped keys.
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Lattice position of a fixed-point coordinate on n cells: p = m n / 2^24,
+// base = min(floor(p), n - 1), frac = p - base (exact in float).
+__device__ __forceinline__ void lattice(uint32_t m, uint32_t n, uint32_t& base, float& frac) {
+  const uint64_t p = (uint64_t)m * n;
+  uint32_t b = (uint32_t)(p >> 24);
+  b = b < n - 1 ? b : n - 1;
+  base = b;
+  frac = (float)(uint32_t)(p - ((uint64_t)b << 24)) * (1.0f / 16777216.0f);
+}
+
+// Table index of vertex (x, y, z) of level l: dense x + y(N+1) + z(N+1)^2,
+// hashed (x * 1 xor y * 2654435761 xor z * 805459861) mod T (Mueller et al.).
+__device__ __forceinline__ uint32_t corner_index(const LevelTab& lv, int l, uint32_t x, uint32_t y,
+                                                 uint32_t z) {
+  if ((lv.dense_mask >> l) & 1u) {
+    const uint32_t s = lv.N[l] + 1u;
+    return x + s * (y + s * z);
+  }
+  return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & lv.hash_mask;
+}
+
+// Sampling parameters of one model slot in one step (Sec. 3.2-3.3).
+struct SampleParams {
+  uint2 key;           // seed
+  uint32_t model;      // model slot
+  int32_t n_bnd;       // floor(lambda batch) boundary samples first
+  const int32_t* qtab; // half-normal quantile table, kQTab + 1 knots
+};
+
+// Fixed-point coordinates of sample i of iteration `iter`.
+__device__ __forceinline__ uint3 draw_sample(const SampleParams& sp, uint32_t i, uint32_t iter) {
+  if ((int32_t)i >= sp.n_bnd) {
+    const uint4 r = philox(make_uint4(i, iter, sp.model, kPurposeSample), sp.key);
+    return make_uint3(r.x >> 8, r.y >> 8, r.z >> 8);
+  }
+  for (uint32_t attempt = 0;; ++attempt) {
+    const uint4 r = philox(make_uint4(i, iter, sp.model, kPurposeSample + attempt), sp.key);
+    const uint32_t face = __umulhi(r.x, 6u);
+    const uint32_t axis = face >> 1, side = face & 1u;
+    const uint32_t u24 = r.y >> 8, k = u24 >> 12, fr = u24 & 4095u;
+    const int64_t q0 = __ldg(sp.qtab + k), q1 = __ldg(sp.qtab + k + 1);
+    int64_t off = q0 + (((q1 - q0) * (int64_t)fr) >> 12);
+    if (off > (int64_t)kFixOne && attempt < 255) continue;
+    if (off > (int64_t)kFixOne) off = kFixOne;
+    const uint32_t c = side ? kFixOne - (uint32_t)off : (uint32_t)off;
+    const uint32_t a = r.z >> 8, b = r.w >> 8;
+    if (axis == 0) return make_uint3(c, a, b);
+    if (axis == 1) return make_uint3(a, c, b);
+    return make_uint3(a, b, c);
+  }
+}
+
+// Trilinear lookup of a stored block at a fixed-point coordinate: position
+// u (n - 1) per axis (the block spans [0,1] between its outer voxel centres).
+__device__ __forceinline__ float volume_trilinear(const float* __restrict__ vol, int nx, int ny,
+                                                  int nz, uint3 m) {
+  uint32_t bx, by, bz;
+  float fx, fy, fz;
+  lattice(m.x, (uint32_t)(nx - 1), bx, fx);
+  lattice(m.y, (uint32_t)(ny - 1), by, fy);
+  lattice(m.z, (uint32_t)(nz - 1), bz, fz);
+  const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
+  const float* p = vol + bz * sz + by * sy + bx;
+  const float v000 = __ldg(p), v100 = __ldg(p + 1), v010 = __ldg(p + sy), v110 = __ldg(p + sy + 1);
+  const float v001 = __ldg(p + sz), v101 = __ldg(p + sz + 1), v011 = __ldg(p + sz + sy),
+              v111 = __ldg(p + sz + sy + 1);
+  const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+  return gz * (gy * (gx * v000 + fx * v100) + fy * (gx * v010 + fx * v110)) +
+         fz * (gy * (gx * v001 + fx * v101) + fy * (gx * v011 + fx * v111));
+}
+
+__device__ __forceinline__ void value_range(const ModelState* st, float& vmin, float& inv_range) {
+  vmin = ordered_to_float(st->enc_min);
+  const float vmax = ordered_to_float(st->enc_max);
+  inv_range = vmax > vmin ? 1.0f / (vmax - vmin) : 0.0f;
+}
+#endif  // __CUDACC__
+
+// -------------------------------------------------------------- launchers ---
+// Model-independent kernels (util.cu)
+dvnr_status launch_init_params(dvnr_model m, uint64_t seed, cudaStream_t s);
+dvnr_status launch_refresh_half(dvnr_model m, cudaStream_t s);
+dvnr_status launch_minmax(const float* vol, int64_t n, ModelState* st, cudaStream_t s);
+dvnr_status launch_error_stats(const float* a, const float* b, int64_t n, double* out_dev,
+                               cudaStream_t s);
+dvnr_status launch_corner_indices(dvnr_model m, const uint32_t* coords, int64_t n, uint32_t* idx,
+                                  cudaStream_t s);
+
+struct AdamModelPtrs {
+  float* theta;
+  float* m1;
+  float* m2;
+  float* grad;
+  __half* theta16;
+  ModelState* st;
+};
+struct AdamHyper {
+  float lr, beta1, beta2, eps, weight_decay;
+  float inv_batch;
+  int32_t mixed, growth_interval;
+};
+dvnr_status launch_adam(const AdamModelPtrs* models_dev, int n_models, int64_t n_params,
+                        const AdamHyper& h, cudaStream_t s);
+
+// Plain FP32 path (fp32_path.cu)
+struct Fp32StepArgs {
+  dvnr_model m;
+  const float* vol;
+  SampleParams sp;
+  int32_t batch;
+  int32_t loss;
+  bool explicit_iter;
+  uint32_t iter;
+  // optional debug outputs
+  float* y_out;
+  float* dx0_out;
+  float* tgt_out;
+  uint32_t* coords_out;
+};
+dvnr_status fp32_ensure_workspace(dvnr_model m, int64_t batch);
+dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s);
+dvnr_status fp32_decode_unit(dvnr_model m, const uint32_t* coords, const float* xyz, int64_t n,
+                             int grid_mode, float* out, cudaStream_t s);
+
+// Render (render.cu)
+struct RenderBlock {
+  float lo[3], hi[3];  // owned box, global voxel indices
+  int32_t e[3];        // owned voxels per axis
+  int32_t pad;
+  const float* grid;   // decoded owned grid, x fastest
+};
+dvnr_status launch_render(const RenderBlock* blocks_dev, int n_blocks, const float lo[3],
+                          const float hi[3], const dvnr_tf& tf, int w, int h, int spr,
+                          float* rgba, cudaStream_t s);
+dvnr_status launch_state_reset(ModelState* st, float loss_scale, cudaStream_t s);
+dvnr_status launch_state_reset_scale(ModelState* st, float loss_scale, cudaStream_t s);
+dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_batch, float* grad_out,
+                               float* loss_out, cudaStream_t s);
+
+}  // namespace dvnr

@@ -1,0 +1,31 @@
+// mp_path.cuh -- the FP16 tensor-core (tcgen05) path of libdvnr: grouped
+// persistent training kernel over many models and forward-only decoding.
+#pragma once
+
+#include "dvnr_internal.cuh"
+
+namespace dvnr {
+
+struct MpStepDebug {
+  float* y;
+  float* dx0;
+  float* target;
+  uint32_t* coords;
+};
+
+// True when the model's configuration is one the FP16 kernels are built for.
+bool mp_supported(const dvnr_model m);
+// Free the FP16-path resources of a model (graphs, descriptor tables).
+void mp_release(dvnr_model m);
+// cfg->steps grouped steps of all n models (one fused kernel + Adam per step).
+dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const dvnr_train_cfg* cfg,
+                     const AdamHyper& h, cudaStream_t s);
+// One forward/backward of model slot 0 at iteration `iter` and loss scale S,
+// gradients left (scaled by S) in m->grad.
+dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* cfg, uint32_t iter,
+                          float S, const MpStepDebug& dbg, cudaStream_t s);
+// FP16 inference: xyz points (grid_mode 0) or the owned grid (grid_mode 1).
+dvnr_status mp_decode(dvnr_model m, const float* xyz, int64_t n, int grid_mode, float* out,
+                      cudaStream_t s);
+
+}  // namespace dvnr

@@ -1,0 +1,87 @@
+// profile.cu -- launch counting and optional CUDA-event timing of every
+// library kernel (used by the benchmark to measure kernel durations on the
+// stream each kernel runs on).
+#include <atomic>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dvnr_internal.cuh"
+
+namespace dvnr {
+
+namespace {
+struct Record {
+  std::string name;
+  cudaEvent_t a, b;
+};
+std::mutex g_mu;
+std::vector<Record> g_records;
+std::atomic<bool> g_on{false};
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+bool profiling_on() { return g_on.load(); }
+void count_launches(int64_t n) { g_launches.fetch_add(n); }
+
+ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  g_launches.fetch_add(1);
+  if (!g_on.load()) return;
+  if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
+    cudaGetLastError();
+    a_ = b_ = nullptr;
+    return;
+  }
+  cudaEventRecord(a_, s_);
+}
+
+ProfScope::~ProfScope() {
+  if (!a_) return;
+  cudaEventRecord(b_, s_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_records.push_back({name_, a_, b_});
+}
+
+}  // namespace dvnr
+
+using namespace dvnr;
+
+extern "C" {
+
+dvnr_status dvnr_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& r : g_records) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_records.clear();
+  g_on.store(on != 0);
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_profile_read(const char* kernel, double* total_ms, int64_t* launches) {
+  if (!kernel || !total_ms || !launches) {
+    set_error("NULL argument");
+    return DVNR_E_INVALID;
+  }
+  DVNR_CUDA(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> lk(g_mu);
+  double t = 0.0;
+  int64_t n = 0;
+  const bool all = std::strcmp(kernel, "*") == 0;
+  for (auto& r : g_records) {
+    if (!all && r.name != kernel) continue;
+    float ms = 0.f;
+    DVNR_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    t += ms;
+    ++n;
+  }
+  *total_ms = t;
+  *launches = n;
+  return DVNR_OK;
+}
+
+int64_t dvnr_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,389 @@
+// util.cu -- initialisation, value-range pre-pass, fused Adam, FP64 error
+// reduction and the corner-index probe of libdvnr.
+#include <cstring>
+
+#include "dvnr_internal.cuh"
+
+namespace dvnr {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+int grid_for(int64_t n, int threads, int cap = 152 * 16) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  return (int)(g < cap ? g : cap);
+}
+
+// Parameter initialisation (the paper is silent; Mueller et al. tables
+// U(-1e-4, 1e-4), Glorot-uniform MLP). u = (r0 >> 8) 2^-24 from Philox block
+// {i_lo, i_hi, 0, 'INIT'} keyed by the seed; v = lo + (hi - lo) u computed in
+// FP64 with explicit round-to-nearest operations, then rounded to binary32.
+struct InitArgs {
+  float* theta;
+  __half* theta16;
+  int64_t n_params, n_enc;
+  int64_t bound[kMaxHidden + 1];  // end (exclusive) of matrix k
+  double limit[kMaxHidden + 1];
+  int32_t n_mats;
+  uint2 key;
+};
+
+__global__ void k_init_params(InitArgs a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_params;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 r = philox(make_uint4((uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0u, kPurposeInit),
+                           a.key);
+    const double u = (double)(r.x >> 8) * (1.0 / 16777216.0);
+    double lo, hi;
+    if (i < a.n_enc) {
+      lo = -1e-4;
+      hi = 1e-4;
+    } else {
+      int k = 0;
+      while (k < a.n_mats - 1 && i >= a.bound[k]) ++k;
+      lo = -a.limit[k];
+      hi = a.limit[k];
+    }
+    const double span = __dsub_rn(hi, lo);
+    const double v = __dadd_rn(lo, __dmul_rn(span, u));
+    const float f = __double2float_rn(v);
+    a.theta[i] = f;
+    a.theta16[i] = __float2half_rn(f);
+  }
+}
+
+__global__ void k_refresh_half(const float* __restrict__ theta, __half* __restrict__ theta16,
+                               int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    theta16[i] = __float2half_rn(theta[i]);
+}
+
+// Value range of a training volume (Sec. 3.1 normalises values by the
+// partition's min and max, ghost layer included) and a NaN/Inf check.
+__global__ void k_minmax(const float* __restrict__ v, int64_t n, ModelState* st) {
+  float lo = INFINITY, hi = -INFINITY;
+  uint32_t bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = __ldg(v + i);
+    if (!isfinite(x)) {
+      bad = 1;
+      continue;
+    }
+    lo = fminf(lo, x);
+    hi = fmaxf(hi, x);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lo <= hi) {
+      atomicMin(&st->enc_min, float_to_ordered(lo));
+      atomicMax(&st->enc_max, float_to_ordered(hi));
+    }
+    if (bad) atomicOr(&st->nonfinite, 1u);
+  }
+}
+
+// FP64 reduction of sum (a-b)^2 and max |a-b| (Sec. 5: PSNR from the MSE).
+__global__ void k_error_stats(const float* __restrict__ a, const float* __restrict__ b, int64_t n,
+                              double* out) {
+  double s = 0.0, mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (double)__ldg(a + i) - (double)__ldg(b + i);
+    s += d * d;
+    mx = fmax(mx, fabs(d));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __shared__ double ss[kThreads / 32], sm[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    ss[threadIdx.x >> 5] = s;
+    sm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, m = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      t += ss[w];
+      m = fmax(m, sm[w]);
+    }
+    atomicAdd(out, t);
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long*>(out + 1),
+              (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+__global__ void k_corner_indices(LevelTab lv, const uint32_t* __restrict__ coords, int64_t n,
+                                 uint32_t* __restrict__ idx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t mx = coords[3 * i], my = coords[3 * i + 1], mz = coords[3 * i + 2];
+    for (int l = 0; l < lv.L; ++l) {
+      uint32_t bx, by, bz;
+      float f;
+      lattice(mx, lv.N[l], bx, f);
+      lattice(my, lv.N[l], by, f);
+      lattice(mz, lv.N[l], bz, f);
+      for (int k = 0; k < 8; ++k)
+        idx[(i * lv.L + l) * 8 + k] =
+            corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+    }
+  }
+}
+
+// Fused Adam over every parameter of every model of a step (Sec. 3.6:
+// beta1, beta2, eps, L2 weight decay added to the gradient; Kingma & Ba bias
+// correction). One HBM pass: read grad, theta, m, v; write theta, m, v, the
+// FP16 copy and a zeroed grad. A step whose gradient held a non-finite value
+// (flag set by the training kernels) is skipped and, on the FP16 path, halves
+// the loss scale; growth_interval finite steps double it. The last block of
+// each model updates the model's step counters.
+__global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restrict__ models,
+                                                   int64_t n, AdamHyper h) {
+  const AdamModelPtrs md = models[blockIdx.y];
+  ModelState* st = md.st;
+  const bool skip = *((volatile uint32_t*)&st->overflow) != 0u;
+  const float S = h.mixed ? st->loss_scale : 1.0f;
+  const float inv_S = 1.0f / S;
+  const uint32_t t = st->adam_t + 1u;
+  const float bc1 = 1.0f - powf(h.beta1, (float)t);
+  const float bc2 = 1.0f - powf(h.beta2, (float)t);
+  const float ib1 = 1.0f - h.beta1, ib2 = 1.0f - h.beta2;
+  const int64_t n4 = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float4* g4 = reinterpret_cast<float4*>(md.grad);
+  if (!skip) {
+    float4* th4 = reinterpret_cast<float4*>(md.theta);
+    float4* m14 = reinterpret_cast<float4*>(md.m1);
+    float4* m24 = reinterpret_cast<float4*>(md.m2);
+    for (int64_t i = tid; i < n4; i += stride) {
+      float4 g = g4[i], th = th4[i], a = m14[i], b = m24[i];
+      float* gp = &g.x;
+      float* tp = &th.x;
+      float* ap = &a.x;
+      float* bp = &b.x;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float gg = gp[j] * inv_S + h.weight_decay * tp[j];
+        ap[j] = h.beta1 * ap[j] + ib1 * gg;
+        bp[j] = h.beta2 * bp[j] + ib2 * gg * gg;
+        tp[j] -= h.lr * (ap[j] / bc1) / (sqrtf(bp[j] / bc2) + h.eps);
+      }
+      th4[i] = th;
+      m14[i] = a;
+      m24[i] = b;
+      g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __half2* h2 = reinterpret_cast<__half2*>(md.theta16) + 2 * i;
+      h2[0] = __floats2half2_rn(th.x, th.y);
+      h2[1] = __floats2half2_rn(th.z, th.w);
+    }
+    for (int64_t i = 4 * n4 + tid; i < n; i += stride) {
+      const float gg = md.grad[i] * inv_S + h.weight_decay * md.theta[i];
+      const float a = h.beta1 * md.m1[i] + ib1 * gg;
+      const float b = h.beta2 * md.m2[i] + ib2 * gg * gg;
+      const float th = md.theta[i] - h.lr * (a / bc1) / (sqrtf(b / bc2) + h.eps);
+      md.m1[i] = a;
+      md.m2[i] = b;
+      md.theta[i] = th;
+      md.theta16[i] = __float2half_rn(th);
+      md.grad[i] = 0.f;
+    }
+  } else {
+    for (int64_t i = tid; i < n4; i += stride) g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t i = 4 * n4 + tid; i < n; i += stride) md.grad[i] = 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t done = atomicAdd(&st->done_blocks, 1u);
+    if (done == gridDim.x - 1) {
+      __threadfence();
+      if (skip) {
+        st->skipped += 1u;
+        st->good_steps = 0u;
+        if (h.mixed) st->loss_scale = S * 0.5f;
+      } else {
+        st->adam_t = t;
+        if (h.mixed) {
+          const uint32_t gs = st->good_steps + 1u;
+          if ((int32_t)gs >= h.growth_interval) {
+            st->loss_scale = S * 2.0f;
+            st->good_steps = 0u;
+          } else {
+            st->good_steps = gs;
+          }
+        }
+      }
+      st->last_loss = st->loss_sum * h.inv_batch;
+      st->loss_sum = 0.f;
+      st->overflow = 0u;
+      st->iter += 1u;
+      st->done_blocks = 0u;
+    }
+  }
+}
+
+// Reset the optimiser counters of a model, keeping its value range.
+__global__ void k_state_reset(ModelState* st, float loss_scale) {
+  st->nonfinite = 0u;
+  st->overflow = 0u;
+  st->loss_scale = loss_scale;
+  st->good_steps = 0u;
+  st->iter = 0u;
+  st->adam_t = 0u;
+  st->skipped = 0u;
+  st->done_blocks = 0u;
+  st->loss_sum = 0.f;
+  st->last_loss = 0.f;
+  st->timeouts = 0u;
+}
+
+// Hand out the gradient of one forward/backward without an optimiser step:
+// grad_out = grad / S, loss_out = loss_sum / B; then clear the accumulators.
+__global__ void k_finish_grad(float* __restrict__ grad, int64_t n, float inv_S,
+                              float* __restrict__ grad_out, ModelState* st, float inv_batch,
+                              float* __restrict__ loss_out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (grad_out) grad_out[i] = grad[i] * inv_S;
+    grad[i] = 0.f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t done = atomicAdd(&st->done_blocks, 1u);
+    if (done == gridDim.x - 1) {
+      if (loss_out) *loss_out = st->loss_sum * inv_batch;
+      st->loss_sum = 0.f;
+      st->overflow = 0u;
+      st->done_blocks = 0u;
+    }
+  }
+}
+
+__global__ void k_state_set_scale(ModelState* st, float loss_scale) {
+  st->loss_scale = loss_scale;
+  st->good_steps = 0u;
+}
+
+}  // namespace
+
+dvnr_status launch_state_reset_scale(ModelState* st, float loss_scale, cudaStream_t s) {
+  {
+    ProfScope ps_("state_reset", s);
+    k_state_set_scale<<<1, 1, 0, s>>>(st, loss_scale);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_state_reset(ModelState* st, float loss_scale, cudaStream_t s) {
+  {
+    ProfScope ps_("state_reset", s);
+    k_state_reset<<<1, 1, 0, s>>>(st, loss_scale);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_batch, float* grad_out,
+                               float* loss_out, cudaStream_t s) {
+  {
+    ProfScope ps_("finish_grad", s);
+    k_finish_grad<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(
+      m->grad, m->n_params, 1.0f / loss_scale_used, grad_out, m->st, inv_batch, loss_out);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_init_params(dvnr_model m, uint64_t seed, cudaStream_t s) {
+  InitArgs a;
+  a.theta = m->theta;
+  a.theta16 = m->theta16;
+  a.n_params = m->n_params;
+  a.n_enc = m->n_enc;
+  a.n_mats = m->mlp.n_hidden + 1;
+  for (int k = 0; k <= m->mlp.n_hidden; ++k) {
+    a.bound[k] = (k < m->mlp.n_hidden) ? m->w_off[k + 1] : m->n_params;
+    a.limit[k] = m->glorot[k];
+  }
+  a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  {
+    ProfScope ps_("init_params", s);
+    k_init_params<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(a);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_refresh_half(dvnr_model m, cudaStream_t s) {
+  {
+    ProfScope ps_("refresh_half", s);
+    k_refresh_half<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(m->theta, m->theta16,
+                                                                     m->n_params);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_minmax(const float* vol, int64_t n, ModelState* st, cudaStream_t s) {
+  DVNR_CUDA(cudaMemsetAsync(&st->enc_min, 0xFF, sizeof(uint32_t), s));
+  DVNR_CUDA(cudaMemsetAsync(&st->enc_max, 0x00, sizeof(uint32_t), s));
+  DVNR_CUDA(cudaMemsetAsync(&st->nonfinite, 0x00, sizeof(uint32_t), s));
+  {
+    ProfScope ps_("minmax", s);
+    k_minmax<<<grid_for(n, kThreads), kThreads, 0, s>>>(vol, n, st);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_error_stats(const float* a, const float* b, int64_t n, double* out_dev,
+                               cudaStream_t s) {
+  DVNR_CUDA(cudaMemsetAsync(out_dev, 0, 2 * sizeof(double), s));
+  {
+    ProfScope ps_("error_stats", s);
+    if (n > 0) k_error_stats<<<grid_for(n, kThreads), kThreads, 0, s>>>(a, b, n, out_dev);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_corner_indices(dvnr_model m, const uint32_t* coords, int64_t n, uint32_t* idx,
+                                  cudaStream_t s) {
+  {
+    ProfScope ps_("corner_indices", s);
+    if (n > 0) k_corner_indices<<<grid_for(n, kThreads), kThreads, 0, s>>>(m->lv, coords, n, idx);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_adam(const AdamModelPtrs* models_dev, int n_models, int64_t n_params,
+                        const AdamHyper& h, cudaStream_t s) {
+  // ~4 blocks of 256 threads per SM over all models
+  int per_model = (int)((152 * 8 + n_models - 1) / n_models);
+  const int64_t need = (n_params / 4 + kThreads - 1) / kThreads;
+  if (per_model > need) per_model = (int)(need > 0 ? need : 1);
+  dim3 grid(per_model, n_models);
+  {
+    ProfScope ps_("adam", s);
+    k_adam<<<grid, kThreads, 0, s>>>(models_dev, n_params, h);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+}  // namespace dvnr

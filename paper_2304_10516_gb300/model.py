@@ -1,0 +1,217 @@
+"""Python front end of libdvnr: a Model handle and thin wrappers around the
+C ABI calls. Tensors are torch tensors on the CUDA device (PyTorch supplies
+device memory and streams only); every computation runs in libdvnr.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _abi as A
+
+
+@dataclass
+class EncodingConfig:
+    """Hash-grid encoding (the paper's appendix keys n_levels,
+    n_features_per_level, log2_hashmap_size, base_resolution, per_level_scale)."""
+    n_levels: int = 16
+    n_features: int = 2
+    log2_T: int = 19
+    base_res: int = 16
+    growth: float = 1.38
+
+
+@dataclass
+class MLPConfig:
+    """ReLU MLP (appendix keys n_neurons, n_hidden_layers)."""
+    width: int = 64
+    n_hidden: int = 3
+
+
+@dataclass
+class TrainConfig:
+    """Training settings (Sec. 3.2-3.3, 3.6 defaults)."""
+    batch: int = 1 << 14
+    steps: int = 1
+    lr: float = 1e-2
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+    weight_decay: float = 1e-9
+    lambda_bnd: float = 0.0
+    sigma_bnd: float = 0.005
+    precision: int = A.DVNR_FP32
+    loss: int = A.DVNR_LOSS_L1
+    growth_interval: int = 2000
+    seed: int = 0
+
+    def to_c(self) -> A.dvnr_train_cfg:
+        return A.dvnr_train_cfg(self.lr, self.beta1, self.beta2, self.eps, self.weight_decay,
+                                self.lambda_bnd, self.sigma_bnd, self.batch, self.precision,
+                                self.loss, self.growth_interval, self.steps, self.seed)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Model:
+    """One INR of a box partition (Sec. 3.1)."""
+
+    def __init__(self, lo, hi, ghost=0, enc: EncodingConfig | None = None,
+                 mlp: MLPConfig | None = None, seed: int = 0):
+        enc = enc or EncodingConfig()
+        mlp = mlp or MLPConfig()
+        self.lo, self.hi, self.ghost = tuple(int(v) for v in lo), tuple(int(v) for v in hi), int(ghost)
+        self.enc, self.mlp = enc, mlp
+        box = A.dvnr_box((C.c_int64 * 3)(*self.lo), (C.c_int64 * 3)(*self.hi), self.ghost)
+        ec = A.dvnr_enc_cfg(enc.n_levels, enc.n_features, enc.log2_T, enc.base_res, float(enc.growth))
+        mc = A.dvnr_mlp_cfg(mlp.width, mlp.n_hidden)
+        h = C.c_void_p()
+        A.call("dvnr_create", C.byref(box), C.byref(ec), C.byref(mc), int(seed), C.byref(h))
+        self._h = h
+        ne, nm = C.c_int64(), C.c_int64()
+        A.call("dvnr_param_count", h, C.byref(ne), C.byref(nm))
+        self.n_enc, self.n_mlp = ne.value, nm.value
+        self.n_params = self.n_enc + self.n_mlp
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "_h", None):
+            A.load().dvnr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def stored_dims(self):
+        return tuple(h - l + 2 * self.ghost for l, h in zip(self.lo, self.hi))
+
+    @property
+    def owned_dims(self):
+        return tuple(h - l for l, h in zip(self.lo, self.hi))
+
+    # -------------------------------------------------------------- weights
+    def get_weights(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        A.call("dvnr_get_weights", self._h, out.ctypes.data, self.n_params)
+        return out
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.n_params
+        A.call("dvnr_set_weights", self._h, w.ctypes.data, self.n_params)
+
+    def copy_weights_from(self, src: "Model", stream=None):
+        A.call("dvnr_copy_weights", self._h, src._h, _stream(stream))
+
+    def set_precision(self, precision: int, stream=None):
+        A.call("dvnr_set_precision", self._h, int(precision), _stream(stream))
+
+    def state(self) -> dict:
+        s = A.dvnr_state_info()
+        A.call("dvnr_get_state", self._h, C.byref(s))
+        return {k: getattr(s, k) for k, _ in A.dvnr_state_info._fields_}
+
+    # ------------------------------------------------------------ training
+    def train_grad(self, volume, cfg: TrainConfig, iteration: int = 0, stream=None,
+                   want=("grad", "y", "target", "dx0", "coords", "loss")):
+        """One step's forward+backward without the optimiser; returns the
+        requested device tensors (unscaled gradients)."""
+        import torch
+
+        dev = volume.device
+        B = cfg.batch
+        D = self.enc.n_levels * self.enc.n_features
+        shapes = {"grad": (self.n_params,), "y": (B,), "target": (B,), "dx0": (B, D),
+                  "coords": (B, 3), "loss": (1,)}
+        outs = {}
+        for k in want:
+            dt = torch.int32 if k == "coords" else torch.float32
+            outs[k] = torch.empty(shapes[k], dtype=dt, device=dev)
+        so = A.dvnr_step_outputs(*[outs[k].data_ptr() if k in outs else None
+                                   for k in ("grad", "y", "target", "dx0", "coords", "loss")])
+        c = cfg.to_c()
+        A.call("dvnr_train_grad", self._h, _ptr(volume), C.byref(c), int(iteration), C.byref(so),
+               _stream(stream))
+        return outs
+
+    # ------------------------------------------------------------ inference
+    def decode_points(self, xyz, stream=None):
+        import torch
+
+        xyz = xyz.contiguous()
+        out = torch.empty(xyz.shape[0], dtype=torch.float32, device=xyz.device)
+        A.call("dvnr_decode_points", self._h, _ptr(xyz), xyz.shape[0], _ptr(out), _stream(stream))
+        return out
+
+    def decode_grid(self, out=None, stream=None):
+        import torch
+
+        ex, ey, ez = self.owned_dims
+        if out is None:
+            out = torch.empty((ez, ey, ex), dtype=torch.float32, device="cuda")
+        A.call("dvnr_decode_grid", self._h, _ptr(out), _stream(stream))
+        return out
+
+    def corner_indices(self, coords, stream=None):
+        import torch
+
+        coords = coords.contiguous()
+        n = coords.shape[0]
+        out = torch.empty((n, self.enc.n_levels, 8), dtype=torch.int32, device=coords.device)
+        A.call("dvnr_corner_indices", self._h, _ptr(coords), n, _ptr(out), _stream(stream))
+        return out
+
+
+def train(models, volumes, cfg: TrainConfig, stream=None, sync: bool = True):
+    """dvnr_train over ``models`` with their stored-block ``volumes``."""
+    n = len(models)
+    hs = (C.c_void_p * n)(*[m.handle for m in models])
+    vs = (C.c_void_p * n)(*[v.data_ptr() for v in volumes])
+    c = cfg.to_c()
+    losses = (C.c_float * n)() if sync else None
+    A.call("dvnr_train", C.cast(hs, C.c_void_p), n, C.cast(vs, C.c_void_p), C.byref(c),
+           _stream(stream), C.cast(losses, C.c_void_p) if sync else None)
+    return [float(v) for v in losses] if sync else None
+
+
+def make_tf(c0=(0.1, 0.2, 0.6), c1=(1.0, 0.9, 0.2), alpha_max=0.05, v_lo=0.0, v_hi=1.0):
+    return A.dvnr_tf((C.c_float * 3)(*c0), (C.c_float * 3)(*c1), alpha_max, v_lo, v_hi)
+
+
+def render(models, tf, w, h, spr, out=None, stream=None):
+    import torch
+
+    n = len(models)
+    hs = (C.c_void_p * n)(*[m.handle for m in models])
+    if out is None:
+        out = torch.empty((h, w, 4), dtype=torch.float32, device="cuda")
+    A.call("dvnr_render", C.cast(hs, C.c_void_p), n, C.byref(tf), w, h, spr, _ptr(out),
+           _stream(stream))
+    return out
+
+
+def error_stats(a, b, stream=None):
+    """(sum of squared differences, max abs difference) in FP64 on the device."""
+    out = (C.c_double * 2)()
+    A.call("dvnr_error_stats", _ptr(a.contiguous()), _ptr(b.contiguous()), a.numel(),
+           C.cast(out, C.c_void_p), _stream(stream))
+    return out[0], out[1]
