@@ -269,6 +269,14 @@ dvnr_status dvnr_profile_read(const char* kernel, double* total_ms, int64_t* lau
  * graph replay adds the kernel nodes it runs.                              */
 int64_t dvnr_launch_count(void);
 
+/* Diagnostic of the tensor-core operand layouts used by the FP16 path: one
+ * 128 x 64 x 64 tcgen05 product per operand order (A K-major/MN-major x
+ * B K-major/MN-major) on values exact in FP16 and FP32, compared with a SIMT
+ * product. mismatches_host[0..3] receive the number of differing outputs of
+ * each case, mismatches_host[4] is 1 if a bounded wait gave up. Synchronises.
+ * Returns DVNR_E_TIMEOUT if a wait gave up.                                */
+dvnr_status dvnr_selftest_umma(int32_t* mismatches_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -45,6 +45,8 @@ struct ProfScope {
 };
 bool profiling_on();
 void count_launches(int64_t n);
+// Launches recorded into a CUDA graph are counted when the graph is replayed.
+void set_capturing(bool on);
 
 // ----------------------------------------------------------- level table ----
 // Per-level layout of the hash-grid tables (kernel parameter, by value).

@@ -1,21 +1,1180 @@
-// mp_path.cu -- placeholder until the tcgen05 kernels land.
+// mp_path.cu -- the FP16 tensor-core path of libdvnr.
+//
+// Training (Sec. 3.2): one persistent kernel per step trains every model of
+// the call (the paper's one-model-per-partition, Sec. 3.1, as a grouped
+// launch): each CTA walks a contiguous run of 128-sample tiles, and per tile
+//   draw samples (Philox) -> trilinear target -> hash-grid gather (FP16
+//   tables, FP32 interpolation) -> MLP forward on tcgen05 (FP16 operands in
+//   shared memory, FP32 accumulators in TMEM) -> L1/L2 loss with loss scale
+//   -> backward on tcgen05: dL/dH per layer, and the weight gradients of the
+//   whole run accumulated in TMEM -> dL/d(encoding) scattered into the FP32
+//   table gradients with vector atomics.
+// The fused Adam of util.cu follows; a step pair is replayed from a CUDA
+// graph. Decoding (Sec. 3, Sec. 4.1) runs the forward half on the same tiles.
+//
+// Tile buffers in shared memory hold 128 samples x features as FP16 core
+// matrices (8 samples x 8 features, 128 B): feature group g, sample group q
+// at byte ((g * 16) + q) * 128. Read along features they are the K-major A
+// operand of a layer (M = samples); read along samples they are the MN-major
+// operands of the weight-gradient products (K = samples).
+//   ACT: X0 (the encoding, D features), H_1 .. H_{H-1} (W features each)
+//   DZ : dZ_1 .. dZ_H (W features each)
+// dW_k = dZ_{k+1}^T H_k is formed as an M = 128 product whose A operand is
+// the 128 features starting at dZ_{k+1}; rows W..127 of that accumulator
+// collect unused products and are never read.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "mp_path.cuh"
+#include "umma.cuh"
 
 namespace dvnr {
-bool mp_supported(const dvnr_model) { return false; }
-void mp_release(dvnr_model) {}
-dvnr_status mp_train(dvnr_model*, int, const float* const*, const dvnr_train_cfg*, const AdamHyper&,
-                     cudaStream_t) {
-  set_error("FP16 path not built");
-  return DVNR_E_UNSUPPORTED;
+
+namespace {
+
+constexpr int kTile = 128;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s of SM clock per wait
+
+__device__ __forceinline__ uint32_t tile_off(uint32_t f, uint32_t s) {
+  return ((((f >> 3) << 4) + (s >> 3)) << 7) + ((s & 7u) << 4) + ((f & 7u) << 1);
 }
-dvnr_status mp_train_grad(dvnr_model, const float*, const dvnr_train_cfg*, uint32_t, float,
-                          const MpStepDebug&, cudaStream_t) {
-  set_error("FP16 path not built");
-  return DVNR_E_UNSUPPORTED;
+// Weight (out o, in i) of a layer with `out` rows: core matrix (o/8, i/8).
+__device__ __forceinline__ uint32_t wsm_off(uint32_t o, uint32_t i, uint32_t out) {
+  return (((i >> 3) * (out >> 3) + (o >> 3)) << 7) + ((o & 7u) << 4) + ((i & 7u) << 1);
 }
-dvnr_status mp_decode(dvnr_model, const float*, int64_t, int, float*, cudaStream_t) {
-  set_error("FP16 path not built");
-  return DVNR_E_UNSUPPORTED;
+
+struct MpModel {
+  const __half* theta16;
+  float* grad;
+  const float* vol;
+  int32_t nx, ny, nz;
+  uint32_t slot;
+  ModelState* st;
+};
+
+struct MpLayout {
+  uint32_t smem_wout, smem_w, smem_dz, smem_act, smem_bytes;
+  uint32_t wbyte[kMaxHidden + 1];   // byte offset of W_k inside the weight area
+  uint32_t act_off[kMaxHidden];     // feature offset of H_k in ACT (H_0 = X0)
+  uint32_t tmem_cols;
+  uint32_t dw_col[kMaxHidden];      // TMEM column of dW_k
+  int ctas_per_sm;
+};
+
+struct MpParams {
+  LevelTab lv;
+  int32_t D, H;
+  int64_t w_off[kMaxHidden + 1];
+  MpLayout lay;
+  int32_t batch, n_bnd, loss, tiles_per_model;
+  int64_t total_tiles;
+  uint2 key;
+  const int32_t* qtab;
+  const MpModel* models;
+  float inv_batch;
+  int32_t explicit_iter;
+  uint32_t iter;
+  float loss_scale_override;
+  float* dbg_y;
+  float* dbg_dx0;
+  float* dbg_tgt;
+  uint32_t* dbg_coords;
+};
+
+struct MpDecodeParams {
+  LevelTab lv;
+  int32_t D, H;
+  int64_t w_off[kMaxHidden + 1];
+  MpLayout lay;
+  const __half* theta16;
+  const ModelState* st;
+  int64_t n, n_tiles;
+  const float* xyz;
+  int grid_mode;
+  int64_t e[3], nstore[3];
+  int32_t ghost;
+  float origin[3];
+  float* out;
+};
+
+// ---------------------------------------------------------------- gathers --
+template <int F>
+struct HalfVec;
+template <>
+struct HalfVec<1> {
+  static __device__ __forceinline__ void load(const __half* p, float* v) { v[0] = __half2float(__ldg(p)); }
+};
+template <>
+struct HalfVec<2> {
+  static __device__ __forceinline__ void load(const __half* p, float* v) {
+    const __half2 a = __ldg(reinterpret_cast<const __half2*>(p));
+    const float2 f = __half22float2(a);
+    v[0] = f.x;
+    v[1] = f.y;
+  }
+};
+template <>
+struct HalfVec<4> {
+  static __device__ __forceinline__ void load(const __half* p, float* v) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+};
+template <>
+struct HalfVec<8> {
+  static __device__ __forceinline__ void load(const __half* p, float* v) {
+    HalfVec<4>::load(p, v);
+    HalfVec<4>::load(p + 4, v + 4);
+  }
+};
+
+template <int F>
+__device__ __forceinline__ void red_add(float* p, const float* g);
+template <>
+__device__ __forceinline__ void red_add<1>(float* p, const float* g) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(g[0]) : "memory");
 }
+template <>
+__device__ __forceinline__ void red_add<2>(float* p, const float* g) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(g[0]), "f"(g[1]) : "memory");
+}
+template <>
+__device__ __forceinline__ void red_add<4>(float* p, const float* g) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(g[0]), "f"(g[1]),
+               "f"(g[2]), "f"(g[3])
+               : "memory");
+}
+template <>
+__device__ __forceinline__ void red_add<8>(float* p, const float* g) {
+  red_add<4>(p, g);
+  red_add<4>(p + 4, g + 4);
+}
+
+// Store F halves of one sample row (features f0 .. f0+F-1, same 16-byte row).
+template <int F>
+__device__ __forceinline__ void st_row(uint8_t* base, uint32_t off, const float* v) {
+  if (F == 1) {
+    *reinterpret_cast<__half*>(base + off) = __float2half_rn(v[0]);
+  } else if (F == 2) {
+    *reinterpret_cast<__half2*>(base + off) = __floats2half2_rn(v[0], v[1]);
+  } else if (F == 4) {
+    uint2 u;
+    __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    u.x = *reinterpret_cast<uint32_t*>(&a);
+    u.y = *reinterpret_cast<uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(base + off) = u;
+  } else {
+    uint4 u;
+    __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    __half2 c = __floats2half2_rn(v[4], v[5]), d = __floats2half2_rn(v[6], v[7]);
+    u.x = *reinterpret_cast<uint32_t*>(&a);
+    u.y = *reinterpret_cast<uint32_t*>(&b);
+    u.z = *reinterpret_cast<uint32_t*>(&c);
+    u.w = *reinterpret_cast<uint32_t*>(&d);
+    *reinterpret_cast<uint4*>(base + off) = u;
+  }
+}
+
+// Hash-grid encoding of one coordinate, FP16 tables, FP32 interpolation,
+// written as FP16 to the sample's row of the ACT tile (feature 0 .. D-1).
+template <int F>
+__device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half* __restrict__ tab16,
+                                               uint3 m, bool valid, uint8_t* act, uint32_t s) {
+  for (int l = 0; l < lv.L; ++l) {
+    float acc[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) acc[f] = 0.f;
+    if (valid) {
+      uint32_t bx, by, bz;
+      float fx, fy, fz;
+      lattice(m.x, lv.N[l], bx, fx);
+      lattice(m.y, lv.N[l], by, fy);
+      lattice(m.z, lv.N[l], bz, fz);
+      const __half* tab = tab16 + lv.off[l];
+      float v[8][F];
+      uint32_t idx[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        idx[k] = corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) HalfVec<F>::load(tab + (size_t)idx[k] * F, v[k]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
+                        (((k >> 2) & 1) ? fz : 1.f - fz);
+#pragma unroll
+        for (int f = 0; f < F; ++f) acc[f] += w * v[k][f];
+      }
+    }
+    st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
+  }
+}
+
+template <int F>
+__device__ __forceinline__ bool scatter_grad(const LevelTab& lv, float* __restrict__ grad, uint3 m,
+                                             const float* dx0) {
+  bool bad = false;
+  for (int l = 0; l < lv.L; ++l) {
+    uint32_t bx, by, bz;
+    float fx, fy, fz;
+    lattice(m.x, lv.N[l], bx, fx);
+    lattice(m.y, lv.N[l], by, fy);
+    lattice(m.z, lv.N[l], bz, fz);
+    float* tab = grad + lv.off[l];
+    float d[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      d[f] = dx0[l * F + f];
+      bad |= !isfinite(d[f]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
+                      (((k >> 2) & 1) ? fz : 1.f - fz);
+      const uint32_t idx = corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+      float g[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) g[f] = w * d[f];
+      red_add<F>(tab + (size_t)idx * F, g);
+    }
+  }
+  return bad;
+}
+
+// Load one model's FP16 weights into the core-matrix weight area and w_out
+// (as FP32) into s_wout.
+__device__ void load_weights(const __half* __restrict__ theta16, const int64_t* w_off, int D, int H,
+                             int W, const MpLayout& lay, uint8_t* smem) {
+  uint8_t* s_w = smem + lay.smem_w;
+  float* s_wout = reinterpret_cast<float*>(smem + lay.smem_wout);
+  for (int k = 0; k < H; ++k) {
+    const int in = k == 0 ? D : W;
+    const __half* src = theta16 + w_off[k];
+    uint8_t* dst = s_w + lay.wbyte[k];
+    for (int e = threadIdx.x; e < W * in; e += blockDim.x) {
+      const int o = e / in, i = e - o * in;
+      *reinterpret_cast<__half*>(dst + wsm_off(o, i, W)) = src[e];
+    }
+  }
+  for (int j = threadIdx.x; j < W; j += blockDim.x) s_wout[j] = __half2float(theta16[w_off[H] + j]);
+}
+
+// Forward MMA chain of layer k: scratch[0:W) = ACT(k) x W_k^T.
+__device__ __forceinline__ void issue_forward(uint32_t tmem, const uint8_t* smem, const MpLayout& lay,
+                                              int k, int in, int W) {
+  const uint32_t a0 = umma::smem_u32(smem + lay.smem_act) + (lay.act_off[k] >> 3) * 2048u;
+  const uint32_t b0 = umma::smem_u32(smem + lay.smem_w + lay.wbyte[k]);
+  const uint32_t id = umma::idesc_f16(kTile, W, 0, 0);
+  const uint32_t wb = (uint32_t)(W >> 3) * 128u;
+  for (int kk = 0; kk < in / 16; ++kk) {
+    const uint64_t a = umma::sdesc(a0 + kk * 4096u, 2048u, 128u);
+    const uint64_t b = umma::sdesc(b0 + kk * 2u * wb, wb, 128u);
+    umma::mma_f16(tmem, a, b, id, kk > 0);
+  }
+}
+
+// ------------------------------------------------------- training kernel ---
+template <int W, int F>
+__global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ MpParams p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 8);
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(smem + 12);
+  uint8_t* s_act = smem + p.lay.smem_act;
+  uint8_t* s_dz = smem + p.lay.smem_dz;
+  const float* s_wout = reinterpret_cast<const float*>(smem + p.lay.smem_wout);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int D = p.D, H = p.H;
+
+  if (tid == 0) {
+    umma::mbar_init(mbar, 1);
+    *abort_flag = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, p.lay.tmem_cols);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);  // this warp's TMEM lanes
+  uint32_t phase = 0;
+
+  const int64_t g_begin = (p.total_tiles * blockIdx.x) / gridDim.x;
+  const int64_t g_end = (p.total_tiles * (blockIdx.x + 1)) / gridDim.x;
+  int cur = -1;
+  bool first_tile = true;
+  MpModel md{};
+  SampleParams sp;
+  sp.key = p.key;
+  sp.n_bnd = p.n_bnd;
+  sp.qtab = p.qtab;
+  uint32_t iter = 0;
+  float S = 1.f, vmin = 0.f, inv_range = 0.f;
+  constexpr int NOUT = W >= 32 ? W / 32 : 1;
+  float acc_out[NOUT];
+  float loss_acc = 0.f;
+
+  // wait for the tensor core and raise/observe the CTA-wide abort flag
+  auto mma_wait = [&]() -> bool {
+    umma::mbar_wait_bounded(mbar, phase, abort_flag, kWaitCycles);
+    phase ^= 1u;
+    __syncthreads();
+    return *abort_flag == 0u;
+  };
+
+  // write the accumulated weight gradients of the current model
+  auto flush = [&]() {
+    umma::fence_after_sync();
+    if (warp * 32 < W) {
+      const int r = warp * 32 + lane;  // output row of the layer
+      for (int k = 0; k < H; ++k) {
+        const int in = k == 0 ? D : W;
+        float* g = md.grad + p.w_off[k];
+        for (int c = 0; c < in; c += 16) {
+          float v[16];
+          umma::ld16(tl + p.lay.dw_col[k] + c, v);
+          umma::ld_wait();
+          if (r < W) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) atomicAdd(g + (size_t)r * in + c + j, v[j]);
+          }
+        }
+      }
+    }
+    float* gout = md.grad + p.w_off[H];
+    if (W >= 32) {
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) atomicAdd(gout + NOUT * lane + j, acc_out[j]);
+    } else if (!(lane & 1)) {
+      atomicAdd(gout + (lane >> 1), acc_out[0]);
+    }
+    float l = loss_acc;
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if (lane == 0) atomicAdd(&md.st->loss_sum, l);
+    umma::fence_before_sync();
+    __syncthreads();
+  };
+
+  for (int64_t g = g_begin; g < g_end; ++g) {
+    const int model = (int)(g / p.tiles_per_model);
+    const int tile = (int)(g - (int64_t)model * p.tiles_per_model);
+    if (model != cur) {
+      if (cur >= 0) flush();
+      cur = model;
+      md = p.models[model];
+      sp.model = md.slot;
+      iter = p.explicit_iter ? p.iter : md.st->iter;
+      S = p.loss_scale_override > 0.f ? p.loss_scale_override : md.st->loss_scale;
+      value_range(md.st, vmin, inv_range);
+#pragma unroll
+      for (int j = 0; j < NOUT; ++j) acc_out[j] = 0.f;
+      loss_acc = 0.f;
+      first_tile = true;
+      load_weights(md.theta16, p.w_off, D, H, W, p.lay, smem);
+    }
+    // -- sample, target, encode
+    const int i = tile * kTile + tid;
+    const bool valid = i < p.batch;
+    const uint3 mc = valid ? draw_sample(sp, (uint32_t)i, iter) : make_uint3(0u, 0u, 0u);
+    const float target =
+        valid ? (volume_trilinear(md.vol, md.nx, md.ny, md.nz, mc) - vmin) * inv_range : 0.f;
+    encode_to_tile<F>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+
+    // -- forward: H_{k+1} = ReLU(H_k W_k^T)
+    float h[W];
+    uint64_t maskH = 0;
+    for (int k = 0; k < H; ++k) {
+      if (tid == 0) {
+        umma::fence_after_sync();
+        issue_forward(tmem, smem, p.lay, k, k == 0 ? D : W, W);
+        umma::commit(mbar);
+      }
+      if (!mma_wait()) goto teardown;
+      umma::fence_after_sync();
+#pragma unroll
+      for (int c = 0; c < W / 16; ++c) {
+        float v[16];
+        umma::ld16(tl + c * 16, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[c * 16 + j] = v[j];
+      }
+      umma::ld_wait();
+      if (k < H - 1) {
+        const uint32_t f0 = p.lay.act_off[k + 1];
+#pragma unroll
+        for (int c = 0; c < W / 8; ++c) {
+          uint4 u;
+          uint32_t* pu = &u.x;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            __half2 t = __floats2half2_rn(fmaxf(h[c * 8 + 2 * j], 0.f), fmaxf(h[c * 8 + 2 * j + 1], 0.f));
+            pu[j] = *reinterpret_cast<uint32_t*>(&t);
+          }
+          *reinterpret_cast<uint4*>(s_act + tile_off(f0 + c * 8, tid)) = u;
+        }
+        umma::fence_proxy_async();
+      } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          if (h[j] > 0.f) maskH |= 1ull << j;
+          h[j] = __half2float(__float2half_rn(fmaxf(h[j], 0.f)));
+        }
+      }
+      umma::fence_before_sync();
+      __syncthreads();
+    }
+
+    {
+      // -- output, loss, dL/dy (scaled by S)
+      float y = 0.f;
+#pragma unroll
+      for (int j = 0; j < W; ++j) y += h[j] * s_wout[j];
+      float dy = 0.f;
+      if (valid) {
+        const float d = y - target;
+        if (p.loss == DVNR_LOSS_L1) {
+          loss_acc += fabsf(d);
+          dy = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * (S * p.inv_batch);
+        } else {
+          loss_acc += d * d;
+          dy = 2.f * d * (S * p.inv_batch);
+        }
+        if (!isfinite(y)) atomicOr(&md.st->overflow, 1u);
+        if (p.dbg_y && cur == 0) {
+          p.dbg_y[i] = y;
+          p.dbg_tgt[i] = target;
+          p.dbg_coords[3 * i] = mc.x;
+          p.dbg_coords[3 * i + 1] = mc.y;
+          p.dbg_coords[3 * i + 2] = mc.z;
+        }
+      }
+      // dW_out += fp16(dy) h_H, reduced over the warp (reduce-scatter)
+      {
+        const float dy16 = __half2float(__float2half_rn(dy));
+        float v[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) v[j] = dy16 * h[j];
+        int n = W;
+#pragma unroll
+        for (int s = 16; s >= 1; s >>= 1) {
+          if (n > 1) {
+            const bool upper = (lane & s) != 0;
+            const int half = n / 2;
+#pragma unroll
+            for (int j = 0; j < W / 2; ++j) {
+              if (j < half) {
+                const float send = upper ? v[j] : v[j + half];
+                const float keep = upper ? v[j + half] : v[j];
+                v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+              }
+            }
+            n = half;
+          } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], s);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) acc_out[j] += v[j];
+      }
+      // dZ_H = fp16(dy w_out) where z_H > 0
+      const uint32_t f0 = (uint32_t)(H - 1) * W;
+#pragma unroll
+      for (int c = 0; c < W / 8; ++c) {
+        uint4 u;
+        uint32_t* pu = &u.x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int a = c * 8 + 2 * j;
+          const float v0 = ((maskH >> a) & 1ull) ? dy * s_wout[a] : 0.f;
+          const float v1 = ((maskH >> (a + 1)) & 1ull) ? dy * s_wout[a + 1] : 0.f;
+          __half2 t = __floats2half2_rn(v0, v1);
+          pu[j] = *reinterpret_cast<uint32_t*>(&t);
+        }
+        *reinterpret_cast<uint4*>(s_dz + tile_off(f0 + c * 8, tid)) = u;
+      }
+    }
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+
+    // -- backward: layer k maps H_{k-1} -> Z_k with W_{k-1}
+    {
+      float dx0[64];
+      for (int k = H; k >= 1; --k) {
+        const int in = k == 1 ? D : W;
+        if (tid == 0) {
+          umma::fence_after_sync();
+          const uint32_t dz0 = umma::smem_u32(s_dz) + ((uint32_t)((k - 1) * W) >> 3) * 2048u;
+          const uint32_t act0 = umma::smem_u32(s_act) + (p.lay.act_off[k - 1] >> 3) * 2048u;
+          // dW_{k-1} += dZ_k^T H_{k-1} (K = samples; both operands MN-major)
+          const uint32_t idw = umma::idesc_f16(kTile, in, 1, 1);
+          for (int ks = 0; ks < kTile / 16; ++ks) {
+            const uint64_t a = umma::sdesc(dz0 + ks * 256u, 128u, 2048u);
+            const uint64_t b = umma::sdesc(act0 + ks * 256u, 128u, 2048u);
+            umma::mma_f16(tmem + p.lay.dw_col[k - 1], a, b, idw, (first_tile && ks == 0) ? 0u : 1u);
+          }
+          // dH_{k-1} = dZ_k W_{k-1} (A K-major over the W outputs, B MN-major)
+          const uint32_t ibw = umma::idesc_f16(kTile, in, 0, 1);
+          const uint32_t w0 = umma::smem_u32(smem + p.lay.smem_w + p.lay.wbyte[k - 1]);
+          const uint32_t wb = (uint32_t)(W >> 3) * 128u;
+          for (int kk = 0; kk < W / 16; ++kk) {
+            const uint64_t a = umma::sdesc(dz0 + kk * 4096u, 2048u, 128u);
+            const uint64_t b = umma::sdesc(w0 + kk * 256u, 128u, wb);
+            umma::mma_f16(tmem, a, b, ibw, kk > 0);
+          }
+          umma::commit(mbar);
+        }
+        if (!mma_wait()) goto teardown;
+        umma::fence_after_sync();
+        if (k > 1) {
+          float dh[W];
+#pragma unroll
+          for (int c = 0; c < W / 16; ++c) {
+            float v[16];
+            umma::ld16(tl + c * 16, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) dh[c * 16 + j] = v[j];
+          }
+          umma::ld_wait();
+          const uint32_t fa = p.lay.act_off[k - 1], fz = (uint32_t)(k - 2) * W;
+#pragma unroll
+          for (int c = 0; c < W / 8; ++c) {
+            const uint4 hv = *reinterpret_cast<const uint4*>(s_act + tile_off(fa + c * 8, tid));
+            const uint32_t* ph = &hv.x;
+            uint4 u;
+            uint32_t* pu = &u.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const __half2 hh = *reinterpret_cast<const __half2*>(ph + j);
+              const float2 hf = __half22float2(hh);
+              const float v0 = hf.x > 0.f ? dh[c * 8 + 2 * j] : 0.f;
+              const float v1 = hf.y > 0.f ? dh[c * 8 + 2 * j + 1] : 0.f;
+              __half2 t = __floats2half2_rn(v0, v1);
+              pu[j] = *reinterpret_cast<uint32_t*>(&t);
+            }
+            *reinterpret_cast<uint4*>(s_dz + tile_off(fz + c * 8, tid)) = u;
+          }
+          umma::fence_proxy_async();
+          umma::fence_before_sync();
+          __syncthreads();
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            if (c * 16 < D) {
+              float v[16];
+              umma::ld16(tl + c * 16, v);
+#pragma unroll
+              for (int j = 0; j < 16; ++j) dx0[c * 16 + j] = v[j];
+            }
+          }
+          umma::ld_wait();
+          umma::fence_before_sync();
+        }
+      }
+      // -- scatter dL/d(encoding) into the table gradients
+      if (valid) {
+        if (scatter_grad<F>(p.lv, md.grad, mc, dx0)) atomicOr(&md.st->overflow, 1u);
+        if (p.dbg_dx0 && cur == 0) {
+          const float inv_S = 1.0f / S;
+          for (int j = 0; j < D; ++j) p.dbg_dx0[(size_t)i * D + j] = dx0[j] * inv_S;
+        }
+      }
+    }
+    first_tile = false;
+  }
+  if (cur >= 0) flush();
+
+teardown:
+  if (*abort_flag) {
+    // give an MMA still in flight a bounded chance to finish before freeing TMEM
+    if (tid == 0) {
+      const long long t0 = clock64();
+      while (!umma::mbar_try_wait(mbar, phase) && clock64() - t0 < kWaitCycles) {
+      }
+      if (cur >= 0) atomicAdd(&md.st->timeouts, 1u);
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(tmem, p.lay.tmem_cols);
+}
+
+// --------------------------------------------------------- decode kernel ---
+__device__ __forceinline__ uint32_t dec_unit_to_fixed(float g, float origin, int64_t n) {
+  if (n < 2) return 0u;
+  float u = (g - origin) / (float)(n - 1);
+  u = fminf(fmaxf(u, 0.f), 1.f);
+  return (uint32_t)__float2uint_rn(u * 16777216.0f);
+}
+__device__ __forceinline__ uint32_t dec_grid_fixed(int64_t j, int64_t n) {
+  if (n < 2) return 0u;
+  return (uint32_t)((2 * j * (int64_t)kFixOne + (n - 1)) / (2 * (n - 1)));
+}
+
+template <int W, int F>
+__global__ void __launch_bounds__(kTile) k_mp_decode(const __grid_constant__ MpDecodeParams p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 8);
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(smem + 12);
+  uint8_t* s_act = smem + p.lay.smem_act;
+  const float* s_wout = reinterpret_cast<const float*>(smem + p.lay.smem_wout);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int D = p.D, H = p.H;
+  if (tid == 0) {
+    umma::mbar_init(mbar, 1);
+    *abort_flag = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, p.lay.tmem_cols);
+  load_weights(p.theta16, p.w_off, D, H, W, p.lay, smem);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  uint32_t phase = 0;
+  float vmin, inv_range;
+  value_range(p.st, vmin, inv_range);
+  const float range = inv_range > 0.f ? ordered_to_float(p.st->enc_max) - vmin : 0.f;
+
+  for (int64_t t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
+    const int64_t i = t * kTile + tid;
+    const bool valid = i < p.n;
+    uint3 m = make_uint3(0u, 0u, 0u);
+    if (valid) {
+      if (p.grid_mode) {
+        const int64_t x = i % p.e[0], y = (i / p.e[0]) % p.e[1], z = i / (p.e[0] * p.e[1]);
+        m = make_uint3(dec_grid_fixed(x + p.ghost, p.nstore[0]), dec_grid_fixed(y + p.ghost, p.nstore[1]),
+                       dec_grid_fixed(z + p.ghost, p.nstore[2]));
+      } else {
+        m = make_uint3(dec_unit_to_fixed(p.xyz[3 * i], p.origin[0], p.nstore[0]),
+                       dec_unit_to_fixed(p.xyz[3 * i + 1], p.origin[1], p.nstore[1]),
+                       dec_unit_to_fixed(p.xyz[3 * i + 2], p.origin[2], p.nstore[2]));
+      }
+    }
+    encode_to_tile<F>(p.lv, p.theta16, m, valid, s_act, (uint32_t)tid);
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    float h[W];
+    for (int k = 0; k < H; ++k) {
+      if (tid == 0) {
+        umma::fence_after_sync();
+        issue_forward(tmem, smem, p.lay, k, k == 0 ? D : W, W);
+        umma::commit(mbar);
+      }
+      umma::mbar_wait_bounded(mbar, phase, abort_flag, kWaitCycles);
+      phase ^= 1u;
+      __syncthreads();
+      if (*abort_flag) goto teardown;
+      umma::fence_after_sync();
+#pragma unroll
+      for (int c = 0; c < W / 16; ++c) {
+        float v[16];
+        umma::ld16(tl + c * 16, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) h[c * 16 + j] = v[j];
+      }
+      umma::ld_wait();
+      if (k < H - 1) {
+        const uint32_t f0 = p.lay.act_off[k + 1];
+#pragma unroll
+        for (int c = 0; c < W / 8; ++c) {
+          uint4 u;
+          uint32_t* pu = &u.x;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            __half2 q = __floats2half2_rn(fmaxf(h[c * 8 + 2 * j], 0.f), fmaxf(h[c * 8 + 2 * j + 1], 0.f));
+            pu[j] = *reinterpret_cast<uint32_t*>(&q);
+          }
+          *reinterpret_cast<uint4*>(s_act + tile_off(f0 + c * 8, tid)) = u;
+        }
+        umma::fence_proxy_async();
+      } else {
+#pragma unroll
+        for (int j = 0; j < W; ++j) h[j] = __half2float(__float2half_rn(fmaxf(h[j], 0.f)));
+      }
+      umma::fence_before_sync();
+      __syncthreads();
+    }
+    if (valid) {
+      float y = 0.f;
+#pragma unroll
+      for (int j = 0; j < W; ++j) y += h[j] * s_wout[j];
+      p.out[i] = y * range + vmin;
+    }
+  }
+teardown:
+  if (*abort_flag && tid == 0) {
+    const long long t0 = clock64();
+    while (!umma::mbar_try_wait(mbar, phase) && clock64() - t0 < kWaitCycles) {
+    }
+    atomicAdd(const_cast<uint32_t*>(&p.st->timeouts), 1u);
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(tmem, p.lay.tmem_cols);
+}
+
+// ------------------------------------------------------ UMMA self-test -----
+// One 128 x 64 x 64 product per operand-major combination on small integers
+// divided by powers of two (exact in FP16 and FP32), against a SIMT product.
+__global__ void __launch_bounds__(128) k_umma_selftest(int32_t* mismatches) {
+  __shared__ __align__(1024) uint8_t sa[128 * 64 * 2];
+  __shared__ __align__(1024) uint8_t sb[64 * 64 * 2];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ uint32_t abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  auto Aval = [](int m, int k) { return (float)(((m * 3 + k * 5) % 17) - 8) * 0.125f; };
+  auto Bval = [](int k, int n) { return (float)(((k * 7 + n * 11) % 13) - 6) * 0.25f; };
+  if (tid == 0) {
+    umma::mbar_init(&bar, 1);
+    abort_s = 0u;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) umma::tmem_alloc(&tslot, 64);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
+  for (int cs = 0; cs < 4; ++cs) {
+    const int a_mn = cs & 1, b_mn = cs >> 1;
+    // A: M = 128, K = 64. K-major: core (m/8, k/8) at ((k/8)*16 + m/8)*128,
+    // 16-byte rows along K. MN-major: core at ((m/8)*8 + k/8)*128, rows along M.
+    for (int e = tid; e < 128 * 64; e += 128) {
+      const int m = e / 64, k = e % 64;
+      uint32_t off;
+      if (!a_mn)
+        off = ((((k >> 3) << 4) + (m >> 3)) << 7) + ((m & 7) << 4) + ((k & 7) << 1);
+      else
+        off = ((((m >> 3) << 3) + (k >> 3)) << 7) + ((k & 7) << 4) + ((m & 7) << 1);
+      *reinterpret_cast<__half*>(sa + off) = __float2half_rn(Aval(m, k));
+    }
+    // B: K = 64, N = 64. K-major: core at ((k/8)*8 + n/8)*128 rows along K;
+    // MN-major: core at ((n/8)*8 + k/8)*128 rows along N.
+    for (int e = tid; e < 64 * 64; e += 128) {
+      const int k = e / 64, n = e % 64;
+      uint32_t off;
+      if (!b_mn)
+        off = ((((k >> 3) << 3) + (n >> 3)) << 7) + ((n & 7) << 4) + ((k & 7) << 1);
+      else
+        off = ((((n >> 3) << 3) + (k >> 3)) << 7) + ((k & 7) << 4) + ((n & 7) << 1);
+      *reinterpret_cast<__half*>(sb + off) = __float2half_rn(Bval(k, n));
+    }
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      umma::fence_after_sync();
+      const uint32_t a0 = umma::smem_u32(sa), b0 = umma::smem_u32(sb);
+      const uint32_t id = umma::idesc_f16(128, 64, a_mn, b_mn);
+      for (int kk = 0; kk < 4; ++kk) {
+        uint64_t a, b;
+        if (!a_mn) a = umma::sdesc(a0 + kk * 2 * 2048, 2048, 128);   // LBO along K, SBO along M
+        else a = umma::sdesc(a0 + kk * 2 * 128, 128, 1024);          // LBO along K, SBO along M
+        if (!b_mn) b = umma::sdesc(b0 + kk * 2 * 1024, 1024, 128);
+        else b = umma::sdesc(b0 + kk * 2 * 128, 128, 1024);
+        umma::mma_f16(tmem, a, b, id, kk > 0);
+      }
+      umma::commit(&bar);
+    }
+    umma::mbar_wait_bounded(&bar, phase, &abort_s, kWaitCycles);
+    phase ^= 1u;
+    __syncthreads();
+    if (abort_s) break;
+    umma::fence_after_sync();
+    int bad = 0;
+    const int m = tid;
+    for (int c = 0; c < 4; ++c) {
+      float v[16];
+      umma::ld16(tmem + ((uint32_t)(warp * 32) << 16) + c * 16, v);
+      umma::ld_wait();
+      for (int j = 0; j < 16; ++j) {
+        const int n = c * 16 + j;
+        float ref = 0.f;
+        for (int k = 0; k < 64; ++k) ref += Aval(m, k) * Bval(k, n);
+        bad += v[j] != ref;
+      }
+    }
+    atomicAdd(mismatches + cs, bad);
+    umma::fence_before_sync();
+    __syncthreads();
+  }
+  if (abort_s && tid == 0) mismatches[4] = 1;
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(tmem, 64);
+}
+
+// ----------------------------------------------------------- host side -----
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+uint32_t pow2_cols(uint32_t c) {
+  uint32_t p2 = 32;
+  while (p2 < c) p2 <<= 1;
+  return p2;
+}
+
+bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
+  const int W = m->mlp.width, H = m->mlp.n_hidden, D = m->lv.in_dim;
+  lay = MpLayout{};
+  uint32_t off = 64;  // mbarrier, TMEM slot, abort flag, spare
+  lay.smem_wout = off;
+  off += 64 * 4;
+  off = (off + 127) / 128 * 128;
+  lay.smem_w = off;
+  uint32_t wb = 0;
+  for (int k = 0; k < H; ++k) {
+    lay.wbyte[k] = wb;
+    wb += (uint32_t)W * (k == 0 ? D : W) * 2;
+  }
+  off += wb;
+  off = (off + 1023) / 1024 * 1024;
+  const uint32_t feat_bytes = 2048 / 8;  // one feature across 128 samples, per 8-feature group
+  if (train) {
+    lay.smem_dz = off;
+    off += (uint32_t)H * W * feat_bytes;
+  }
+  lay.smem_act = off;
+  lay.act_off[0] = 0;
+  for (int k = 1; k < H; ++k) lay.act_off[k] = (uint32_t)D + (uint32_t)(k - 1) * W;
+  off += ((uint32_t)D + (uint32_t)(H - 1) * W) * feat_bytes;
+  if (train) {
+    // the weight-gradient product of dZ_H reads 128 features from its start
+    const uint32_t need = lay.smem_dz + ((uint32_t)(H - 1) * W + 128) * feat_bytes;
+    off = std::max(off, need);
+  }
+  lay.smem_bytes = (off + 1023) / 1024 * 1024;
+  const uint32_t scratch = (uint32_t)std::max(W, D);
+  uint32_t col = scratch;
+  if (train) {
+    for (int k = 0; k < H; ++k) {
+      lay.dw_col[k] = col;
+      col += (uint32_t)(k == 0 ? D : W);
+    }
+  }
+  lay.tmem_cols = pow2_cols(col);
+  if (lay.tmem_cols > 512 || lay.smem_bytes > 227 * 1024) return false;
+  const int by_smem = (int)((228 * 1024) / (lay.smem_bytes + 1024));
+  const int by_tmem = (int)(512 / lay.tmem_cols);
+  lay.ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_tmem), train ? 2 : 4));
+  return true;
+}
+
+template <int W, int F>
+void set_smem_attr(bool train, uint32_t bytes) {
+  if (train)
+    cudaFuncSetAttribute(k_mp_train<W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  else
+    cudaFuncSetAttribute(k_mp_decode<W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int W, int F>
+void launch_train_wf(const MpParams& p, int grid, cudaStream_t s) {
+  k_mp_train<W, F><<<grid, kTile, p.lay.smem_bytes, s>>>(p);
+}
+template <int W, int F>
+void launch_decode_wf(const MpDecodeParams& p, int grid, cudaStream_t s) {
+  k_mp_decode<W, F><<<grid, kTile, p.lay.smem_bytes, s>>>(p);
+}
+
+#define DVNR_WF_DISPATCH(W, F, FN, ...)                         \
+  do {                                                          \
+    const int w_ = (W), f_ = (F);                               \
+    if (w_ == 16 && f_ == 1) FN<16, 1>(__VA_ARGS__);            \
+    else if (w_ == 16 && f_ == 2) FN<16, 2>(__VA_ARGS__);       \
+    else if (w_ == 16 && f_ == 4) FN<16, 4>(__VA_ARGS__);       \
+    else if (w_ == 16 && f_ == 8) FN<16, 8>(__VA_ARGS__);       \
+    else if (w_ == 32 && f_ == 1) FN<32, 1>(__VA_ARGS__);       \
+    else if (w_ == 32 && f_ == 2) FN<32, 2>(__VA_ARGS__);       \
+    else if (w_ == 32 && f_ == 4) FN<32, 4>(__VA_ARGS__);       \
+    else if (w_ == 32 && f_ == 8) FN<32, 8>(__VA_ARGS__);       \
+    else if (w_ == 64 && f_ == 1) FN<64, 1>(__VA_ARGS__);       \
+    else if (w_ == 64 && f_ == 2) FN<64, 2>(__VA_ARGS__);       \
+    else if (w_ == 64 && f_ == 4) FN<64, 4>(__VA_ARGS__);       \
+    else if (w_ == 64 && f_ == 8) FN<64, 8>(__VA_ARGS__);       \
+  } while (0)
+
+// Per-model cache of the FP16 path: device tables of the last grouped call
+// and its captured CUDA graph.
+struct MpCache {
+  std::vector<dvnr_model> models;
+  std::vector<const float*> vols;
+  dvnr_train_cfg cfg{};
+  int graph_steps = 0;
+  MpModel* d_models = nullptr;
+  AdamModelPtrs* d_adam = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaStream_t cap = nullptr;
+  void clear() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (d_models) cudaFree(d_models);
+    if (d_adam) cudaFree(d_adam);
+    if (cap) cudaStreamDestroy(cap);
+    exec = nullptr;
+    graph = nullptr;
+    d_models = nullptr;
+    d_adam = nullptr;
+    cap = nullptr;
+    models.clear();
+    vols.clear();
+    graph_steps = 0;
+  }
+};
+
+bool same_cfg(const dvnr_train_cfg& a, const dvnr_train_cfg& b) {
+  return a.lr == b.lr && a.beta1 == b.beta1 && a.beta2 == b.beta2 && a.eps == b.eps &&
+         a.weight_decay == b.weight_decay && a.lambda_bnd == b.lambda_bnd &&
+         a.sigma_bnd == b.sigma_bnd && a.batch == b.batch && a.loss == b.loss &&
+         a.growth_interval == b.growth_interval && a.seed == b.seed;
+}
+
+MpParams base_params(const dvnr_model m, const MpLayout& lay, const dvnr_train_cfg* cfg) {
+  MpParams p{};
+  p.lv = m->lv;
+  p.D = m->lv.in_dim;
+  p.H = m->mlp.n_hidden;
+  for (int k = 0; k <= m->mlp.n_hidden; ++k) p.w_off[k] = m->w_off[k];
+  p.lay = lay;
+  p.batch = cfg->batch;
+  p.n_bnd = (int32_t)std::floor((double)cfg->lambda_bnd * (double)cfg->batch);
+  p.loss = cfg->loss;
+  p.tiles_per_model = (cfg->batch + kTile - 1) / kTile;
+  p.key = make_uint2((uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32));
+  p.qtab = m->qtab;
+  p.inv_batch = 1.0f / (float)cfg->batch;
+  return p;
+}
+
+int train_grid(const MpParams& p) {
+  const int64_t cap = (int64_t)sm_count() * p.lay.ctas_per_sm;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(p.total_tiles, cap));
+}
+
+dvnr_status launch_train(const MpParams& p, int W, int F, cudaStream_t s) {
+  ProfScope ps("train_fused_fp16", s);
+  DVNR_WF_DISPATCH(W, F, launch_train_wf, p, train_grid(p), s);
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+}  // namespace
+
+bool mp_supported(const dvnr_model m) {
+  const int D = m->lv.in_dim, W = m->mlp.width, F = m->lv.F;
+  if (!(W == 16 || W == 32 || W == 64)) return false;
+  if (!(F == 1 || F == 2 || F == 4 || F == 8)) return false;
+  if (D % 16 != 0 || D < 16 || D > 64) return false;
+  MpLayout lay;
+  return make_layout(m, true, lay) && make_layout(m, false, lay);
+}
+
+void mp_release(dvnr_model m) {
+  if (m->mp) {
+    MpCache* c = static_cast<MpCache*>(m->mp);
+    c->clear();
+    delete c;
+    m->mp = nullptr;
+  }
+}
+
+dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const dvnr_train_cfg* cfg,
+                     const AdamHyper& h, cudaStream_t s) {
+  dvnr_model m0 = models[0];
+  MpLayout lay;
+  if (!make_layout(m0, true, lay)) {
+    set_error("FP16 path: configuration exceeds shared or tensor memory");
+    return DVNR_E_UNSUPPORTED;
+  }
+  if (!m0->mp) m0->mp = new MpCache();
+  MpCache* c = static_cast<MpCache*>(m0->mp);
+  bool hit = c->d_models && (int)c->models.size() == n && same_cfg(c->cfg, *cfg);
+  for (int i = 0; hit && i < n; ++i) hit = c->models[i] == models[i] && c->vols[i] == vols[i];
+  if (!hit) {
+    if (c->d_models) DVNR_CUDA(cudaStreamSynchronize(s));
+    c->clear();
+    std::vector<MpModel> hm((size_t)n);
+    std::vector<AdamModelPtrs> ha((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      dvnr_model m = models[i];
+      hm[i] = MpModel{m->theta16, m->grad, vols[i], (int32_t)m->dims[0], (int32_t)m->dims[1],
+                      (int32_t)m->dims[2], (uint32_t)i, m->st};
+      ha[i] = AdamModelPtrs{m->theta, m->m1, m->m2, m->grad, m->theta16, m->st};
+    }
+    DVNR_CUDA(cudaMalloc(&c->d_models, sizeof(MpModel) * n));
+    DVNR_CUDA(cudaMalloc(&c->d_adam, sizeof(AdamModelPtrs) * n));
+    DVNR_CUDA(cudaMemcpy(c->d_models, hm.data(), sizeof(MpModel) * n, cudaMemcpyHostToDevice));
+    DVNR_CUDA(cudaMemcpy(c->d_adam, ha.data(), sizeof(AdamModelPtrs) * n, cudaMemcpyHostToDevice));
+    c->models.assign(models, models + n);
+    c->vols.assign(vols, vols + n);
+    c->cfg = *cfg;
+  }
+  MpParams p = base_params(m0, lay, cfg);
+  p.total_tiles = (int64_t)p.tiles_per_model * n;
+  p.models = c->d_models;
+  const int W = m0->mlp.width, F = m0->lv.F;
+  DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
+  auto one_step = [&](cudaStream_t st) -> dvnr_status {
+    dvnr_status rc = launch_train(p, W, F, st);
+    if (rc != DVNR_OK) return rc;
+    return launch_adam(c->d_adam, n, m0->n_params, h, st);
+  };
+  int64_t left = cfg->steps;
+  if (profiling_on() || left < 8) {
+    for (int64_t i = 0; i < left; ++i) {
+      dvnr_status rc = one_step(s);
+      if (rc != DVNR_OK) return rc;
+    }
+    return DVNR_OK;
+  }
+  const int G = 32;  // steps per graph replay
+  if (!c->exec || c->graph_steps != G) {
+    if (c->exec) {
+      cudaGraphExecDestroy(c->exec);
+      cudaGraphDestroy(c->graph);
+      c->exec = nullptr;
+      c->graph = nullptr;
+    }
+    if (!c->cap) DVNR_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    set_capturing(true);
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    dvnr_status rc = DVNR_OK;
+    if (e == cudaSuccess) {
+      for (int g = 0; g < G && rc == DVNR_OK; ++g) rc = one_step(c->cap);
+      cudaError_t e2 = cudaStreamEndCapture(c->cap, &c->graph);
+      if (e == cudaSuccess) e = e2;
+    }
+    set_capturing(false);
+    if (rc != DVNR_OK) return rc;
+    DVNR_CUDA(e);
+    DVNR_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    c->graph_steps = G;
+  }
+  while (left >= G) {
+    DVNR_CUDA(cudaGraphLaunch(c->exec, s));
+    count_launches(2 * G);
+    left -= G;
+  }
+  for (int64_t i = 0; i < left; ++i) {
+    dvnr_status rc = one_step(s);
+    if (rc != DVNR_OK) return rc;
+  }
+  return DVNR_OK;
+}
+
+dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* cfg, uint32_t iter,
+                          float S, const MpStepDebug& dbg, cudaStream_t s) {
+  MpLayout lay;
+  if (!make_layout(m, true, lay)) {
+    set_error("FP16 path: configuration exceeds shared or tensor memory");
+    return DVNR_E_UNSUPPORTED;
+  }
+  MpModel hm{m->theta16, m->grad, vol, (int32_t)m->dims[0], (int32_t)m->dims[1], (int32_t)m->dims[2],
+             0u, m->st};
+  MpModel* d = nullptr;
+  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(MpModel), s));
+  DVNR_CUDA(cudaMemcpyAsync(d, &hm, sizeof(MpModel), cudaMemcpyHostToDevice, s));
+  MpParams p = base_params(m, lay, cfg);
+  p.total_tiles = p.tiles_per_model;
+  p.models = d;
+  p.explicit_iter = 1;
+  p.iter = iter;
+  p.loss_scale_override = S;
+  p.dbg_y = dbg.y;
+  p.dbg_dx0 = dbg.dx0;
+  p.dbg_tgt = dbg.target;
+  p.dbg_coords = dbg.coords;
+  if (!(dbg.y && dbg.target && dbg.coords)) {
+    p.dbg_y = nullptr;  // the per-sample outputs are written together
+  }
+  const int W = m->mlp.width, F = m->lv.F;
+  DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
+  dvnr_status rc = launch_train(p, W, F, s);
+  cudaFreeAsync(d, s);
+  DVNR_CUDA(cudaStreamSynchronize(s));  // the host descriptor is released on return
+  return rc;
+}
+
+dvnr_status mp_decode(dvnr_model m, const float* xyz, int64_t n, int grid_mode, float* out,
+                      cudaStream_t s) {
+  if (n <= 0) return DVNR_OK;
+  MpLayout lay;
+  if (!make_layout(m, false, lay)) {
+    set_error("FP16 path: configuration exceeds shared or tensor memory");
+    return DVNR_E_UNSUPPORTED;
+  }
+  MpDecodeParams p{};
+  p.lv = m->lv;
+  p.D = m->lv.in_dim;
+  p.H = m->mlp.n_hidden;
+  for (int k = 0; k <= m->mlp.n_hidden; ++k) p.w_off[k] = m->w_off[k];
+  p.lay = lay;
+  p.theta16 = m->theta16;
+  p.st = m->st;
+  p.n = n;
+  p.n_tiles = (n + kTile - 1) / kTile;
+  p.xyz = xyz;
+  p.grid_mode = grid_mode;
+  for (int a = 0; a < 3; ++a) {
+    p.e[a] = m->box.hi[a] - m->box.lo[a];
+    p.nstore[a] = m->dims[a];
+    p.origin[a] = (float)(m->box.lo[a] - m->box.ghost);
+  }
+  p.ghost = m->box.ghost;
+  p.out = out;
+  const int W = m->mlp.width, F = m->lv.F;
+  DVNR_WF_DISPATCH(W, F, set_smem_attr, false, lay.smem_bytes);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p.n_tiles, (int64_t)sm_count() * lay.ctas_per_sm));
+  {
+    ProfScope ps("decode_fp16", s);
+    DVNR_WF_DISPATCH(W, F, launch_decode_wf, p, grid, s);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
 }  // namespace dvnr
+
+extern "C" dvnr_status dvnr_selftest_umma(int32_t* mismatches_host) {
+  using namespace dvnr;
+  if (!mismatches_host) {
+    set_error("NULL argument");
+    return DVNR_E_INVALID;
+  }
+  int32_t* d = nullptr;
+  DVNR_CUDA(cudaMalloc(&d, 5 * sizeof(int32_t)));
+  cudaError_t e = cudaMemset(d, 0, 5 * sizeof(int32_t));
+  if (e == cudaSuccess) {
+    ProfScope ps("umma_selftest", 0);
+    k_umma_selftest<<<1, 128>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(mismatches_host, d, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_status(e, "dvnr_selftest_umma");
+  return mismatches_host[4] ? DVNR_E_TIMEOUT : DVNR_OK;
+}

@@ -20,12 +20,15 @@ std::mutex g_mu;
 std::vector<Record> g_records;
 std::atomic<bool> g_on{false};
 std::atomic<int64_t> g_launches{0};
+thread_local bool g_capturing = false;
 }  // namespace
 
 bool profiling_on() { return g_on.load(); }
 void count_launches(int64_t n) { g_launches.fetch_add(n); }
+void set_capturing(bool on) { g_capturing = on; }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  if (g_capturing) return;
   g_launches.fetch_add(1);
   if (!g_on.load()) return;
   if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {

@@ -1,0 +1,216 @@
+"""GPU parity of the FP16 tensor-core path (tcgen05) against the oracle.
+
+The oracle's mixed mode rounds to binary16 at the points where the GPU keeps
+FP16 operands (tables, weights, encoding, hidden activations, scaled output
+gradient, hidden-layer gradients); accumulations stay FP64 there and FP32 on
+the GPU. Tolerances: bit-exact coordinates; forward and gradients within
+2e-3 (normwise for batch sums, plus the kink allowance of parity.py); PSNR
+after seeded training within 0.2 dB of the oracle and of the plain FP32 path.
+"""
+import numpy as np
+import pytest
+
+import parity as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_10516_gb300 import model as dv
+
+    return dv
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2304_10516_gb300 import _abi as A
+
+    return A
+
+
+def _model(dv, c, seed, lo=(0, 0, 0), hi=(64, 64, 64), ghost=0):
+    enc = dv.EncodingConfig(c["L"], c["F"], c["log2T"], c["base"], c["growth"])
+    mlp = dv.MLPConfig(c["width"], c["hidden"])
+    return dv.Model(lo, hi, ghost, enc, mlp, seed=seed)
+
+
+def test_umma_operand_layouts(A):
+    import ctypes as C
+
+    out = (C.c_int32 * 5)()
+    A.call("dvnr_selftest_umma", C.cast(out, C.c_void_p))
+    assert list(out) == [0, 0, 0, 0, 0]
+
+
+CONFIGS = {
+    "blobs64": P.configs_blobs64(),
+    # the 256^3 model's MLP and encoding width with a smaller table
+    "w64d32h3": dict(L=16, F=2, log2T=14, base=16, growth=1.38, width=64, hidden=3, batch=4096),
+    "w16d16h1_f4": dict(L=4, F=4, log2T=12, base=4, growth=1.5, width=16, hidden=1, batch=1000),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("lam,loss", [(0.0, 0), (0.15, 0), (0.0, 1)])
+def test_fp16_step_matches_oracle(dv, orc, A, name, lam, loss):
+    from paper_2304_10516_gb300 import volumes
+
+    c = CONFIGS[name]
+    oc = P.oracle_cfg(c)
+    vol = volumes.blobs(40, seed=1001)
+    theta = P.random_theta(oc, 31, table_scale=0.4)
+    m = _model(dv, c, seed=0, hi=(40, 40, 40))
+    m.set_weights(theta)
+    lam32 = float(np.float32(lam))
+    B = c["batch"]
+    cfg = dv.TrainConfig(batch=B, lambda_bnd=lam32, sigma_bnd=0.005, loss=loss, seed=78,
+                         precision=A.DVNR_FP16)
+    out = m.train_grad(torch.from_numpy(vol).cuda(), cfg, iteration=5)
+    torch.cuda.synchronize()
+    coords = orc.sample(78, 0, 5, B, lam32, orc.quantile_table(float(np.float32(0.005))))
+    np.testing.assert_array_equal(out["coords"].cpu().numpy().view(np.uint32), coords)
+    t = orc.targets(vol, coords, float(vol.min()), float(vol.max()))
+    np.testing.assert_allclose(out["target"].cpu().numpy(), t, atol=2e-6, rtol=0)
+    S = float(2 ** round(np.log2(B)))
+    th64 = theta.astype(np.float64)
+    r = orc.fwd_bwd(oc, th64, coords, t, loss=loss, mixed=True, loss_scale=S, want_zabs=True)
+    y = out["y"].cpu().numpy()
+    np.testing.assert_allclose(y, r["y"], atol=2e-3 * max(1.0, np.abs(r["y"]).max()), rtol=0)
+    a_enc, a_mlp, flagged = P.kink_allowance(oc, th64, coords, t, loss, True, S, B, r["zabs"],
+                                             delta=1e-4)
+    keep = np.ones(B, bool)
+    keep[flagged] = False
+    assert keep.sum() > 0.6 * B
+    P.assert_normwise(out["dx0"].cpu().numpy()[keep], r["dx0"][keep], 2e-3, what="dL/dx0")
+    g = out["grad"].cpu().numpy()
+    P.assert_normwise(g[: oc.n_enc], r["grad_enc"], 2e-3, a_enc, what="table grad")
+    P.assert_normwise(g[oc.n_enc:], r["grad_mlp"], 2e-3, a_mlp, what="mlp grad")
+
+
+def test_fp16_ragged_batch_and_tail(dv, orc, A):
+    # batch not a multiple of the 128-sample tile: the tail rows must not
+    # contribute (compare against the oracle on exactly `batch` samples)
+    from paper_2304_10516_gb300 import volumes
+
+    c = dict(P.configs_blobs64(), batch=333)
+    oc = P.oracle_cfg(c)
+    vol = volumes.blobs(24, seed=1003)
+    theta = P.random_theta(oc, 32, table_scale=0.4)
+    m = _model(dv, c, seed=0, hi=(24, 24, 24))
+    m.set_weights(theta)
+    cfg = dv.TrainConfig(batch=333, loss=1, seed=3, precision=A.DVNR_FP16)
+    out = m.train_grad(torch.from_numpy(vol).cuda(), cfg, iteration=0)
+    coords = orc.sample(3, 0, 0, 333, 0.0, orc.quantile_table(0.005))
+    t = orc.targets(vol, coords, float(vol.min()), float(vol.max()))
+    S = float(2 ** round(np.log2(333)))
+    r = orc.fwd_bwd(oc, theta.astype(np.float64), coords, t, loss=1, mixed=True, loss_scale=S,
+                    want_zabs=True)
+    a_enc, a_mlp, _ = P.kink_allowance(oc, theta.astype(np.float64), coords, t, 1, True, S, 333,
+                                       r["zabs"], delta=1e-4)
+    g = out["grad"].cpu().numpy()
+    P.assert_normwise(g[: oc.n_enc], r["grad_enc"], 2e-3, a_enc, what="table grad")
+    P.assert_normwise(g[oc.n_enc:], r["grad_mlp"], 2e-3, a_mlp, what="mlp grad")
+    assert abs(out["loss"].item() - r["loss"]) < 2e-3 * max(r["loss"], 1e-3)
+
+
+def test_fp16_decode_matches_oracle(dv, orc, A):
+    c = CONFIGS["w64d32h3"]
+    oc = P.oracle_cfg(c)
+    theta = P.random_theta(oc, 7, table_scale=0.3)
+    lo, hi, g = (3, 5, 7), (40, 37, 29), 1
+    m = _model(dv, c, seed=0, lo=lo, hi=hi, ghost=g)
+    m.set_weights(theta)
+    m.set_precision(A.DVNR_FP16)
+    dec = m.decode_grid().cpu().numpy()
+    dims = [h - l + 2 * g for l, h in zip(lo, hi)]
+    want = orc.decode_grid(oc, theta.astype(np.float64), dims, g, 0.0, 1.0, mixed=True)
+    np.testing.assert_allclose(dec, want, atol=2e-3 * max(1.0, np.abs(want).max()), rtol=0)
+    # decode_grid equals point inference at the voxel centres (same kernel path)
+    zz, yy, xx = np.meshgrid(np.arange(lo[2], hi[2]), np.arange(lo[1], hi[1]), np.arange(lo[0], hi[0]),
+                             indexing="ij")
+    xyz = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], 1).astype(np.float32)
+    pts = m.decode_points(torch.from_numpy(xyz).cuda()).cpu().numpy()
+    np.testing.assert_allclose(pts, dec.ravel(), atol=1e-3 * max(1.0, np.abs(want).max()), rtol=0)
+
+
+def _train_psnr(dv, c, vol, seed_model, lr, steps, seed, precision):
+    m = _model(dv, c, seed=seed_model, hi=vol.shape[::-1])
+    cfg = dv.TrainConfig(batch=c["batch"], steps=steps, lr=lr, seed=seed, precision=precision)
+    vt = torch.from_numpy(vol).cuda()
+    losses = dv.train([m], [vt], cfg)
+    sse, _ = dv.error_stats(m.decode_grid(), vt)
+    return P.psnr(sse / vol.size), losses[0], m
+
+
+def test_fp16_training_equal_psnr(dv, orc, A):
+    # 200 seeded steps of the 64^3 workload at lr 1e-3 (non-chaotic regime):
+    # the FP16 path reaches the PSNR of the oracle's FP16 emulation and of
+    # the plain FP32 path within 0.2 dB.
+    from paper_2304_10516_gb300 import volumes
+
+    c = P.configs_blobs64()
+    oc = P.oracle_cfg(c)
+    vol = volumes.blobs(64, seed=1001)
+    p16, l16, m16 = _train_psnr(dv, c, vol, 4242, 1e-3, 200, 99, A.DVNR_FP16)
+    p32, _, _ = _train_psnr(dv, c, vol, 4242, 1e-3, 200, 99, A.DVNR_FP32)
+    st = m16.state()
+    assert st["adam_t"] == 200 and st["skipped"] == 0 and st["precision"] == A.DVNR_FP16
+    th = orc.init_params(oc, 4242)
+    m1, m2 = np.zeros_like(th), np.zeros_like(th)
+    tc = orc.TrainConfig(batch=c["batch"], lr=float(np.float32(1e-3)), seed=99, mixed=True)
+    ost = orc.State(loss_scale=4096.0)
+    orc.train(oc, tc, ost, th, m1, m2, vol, float(vol.min()), float(vol.max()), 200)
+    odec = orc.decode_grid(oc, th, (64, 64, 64), 0, float(vol.min()), float(vol.max()), mixed=True)
+    po = P.psnr(orc.mse(odec, vol)[0])
+    assert abs(p16 - po) < 0.2, (p16, po)
+    assert abs(p16 - p32) < 0.2, (p16, p32)
+
+
+def test_grouped_launch_models_are_independent(dv, A):
+    # Four models in one grouped FP16 launch. Model 0 trained in the group
+    # equals model 0 trained alone (same RNG slot) up to the reordering of
+    # atomic sums, and perturbing model 2's volume leaves the other models
+    # within that same reordering noise.
+    from paper_2304_10516_gb300 import volumes
+
+    c = dict(P.configs_blobs64(), batch=2048)
+    vols = [torch.from_numpy(volumes.blobs(32, seed=2000 + i)).cuda() for i in range(4)]
+
+    def group(vs, steps=10):
+        ms = [_model(dv, c, seed=50 + i, hi=(32, 32, 32)) for i in range(4)]
+        dv.train(ms, vs, dv.TrainConfig(batch=2048, steps=steps, lr=1e-3, seed=5,
+                                        precision=A.DVNR_FP16))
+        return [m.get_weights() for m in ms]
+
+    base = group(vols)
+    again = group(vols)
+    noise = max(np.linalg.norm(a - b) for a, b in zip(base, again))
+    pert = list(vols)
+    pert[2] = vols[2] ** 2  # a non-affine change (min/max normalisation hides affine ones)
+    moved = group(pert)
+    for j in (0, 1, 3):
+        assert np.linalg.norm(moved[j] - base[j]) <= 3 * noise + 1e-6, j
+    assert np.linalg.norm(moved[2] - base[2]) > 10 * noise + 1e-4
+    alone = _model(dv, c, seed=50, hi=(32, 32, 32))
+    dv.train([alone], [vols[0]], dv.TrainConfig(batch=2048, steps=10, lr=1e-3, seed=5,
+                                                precision=A.DVNR_FP16))
+    assert np.linalg.norm(alone.get_weights() - base[0]) <= 3 * noise + 1e-6
+
+
+def test_fp16_overflow_skips_step_and_halves_scale(dv, A):
+    c = dict(P.configs_blobs64(), batch=1024)
+    m = _model(dv, c, seed=1, hi=(16, 16, 16))
+    w = m.get_weights()
+    w[: m.n_enc] = 3.0e4  # encoding outputs near the FP16 limit: activations overflow
+    w[m.n_enc:] = np.abs(w[m.n_enc:]) * 50
+    m.set_weights(w)
+    vol = torch.rand((16, 16, 16), device="cuda")
+    dv.train([m], [vol], dv.TrainConfig(batch=1024, steps=3, precision=A.DVNR_FP16))
+    st = m.state()
+    assert st["skipped"] == 3 and st["adam_t"] == 0
+    assert st["loss_scale"] == 1024.0 / 8
+    np.testing.assert_array_equal(m.get_weights(), w.astype(np.float32))
