@@ -210,21 +210,42 @@ __device__ __forceinline__ uint3 draw_sample(const SampleParams& sp, uint32_t i,
 
 // Trilinear lookup of a stored block at a fixed-point coordinate: position
 // u (n - 1) per axis (the block spans [0,1] between its outer voxel centres).
-__device__ __forceinline__ float volume_trilinear(const float* __restrict__ vol, int nx, int ny,
-                                                  int nz, uint3 m) {
-  uint32_t bx, by, bz;
+// vol_fetch issues the eight corner loads; vol_interp combines them, so the
+// loads can stay in flight while other work runs.
+struct VolCorners {
+  float v[8];
   float fx, fy, fz;
-  lattice(m.x, (uint32_t)(nx - 1), bx, fx);
-  lattice(m.y, (uint32_t)(ny - 1), by, fy);
-  lattice(m.z, (uint32_t)(nz - 1), bz, fz);
+};
+
+__device__ __forceinline__ VolCorners vol_fetch(const float* __restrict__ vol, int nx, int ny, int nz,
+                                                uint3 m) {
+  VolCorners c;
+  uint32_t bx, by, bz;
+  lattice(m.x, (uint32_t)(nx - 1), bx, c.fx);
+  lattice(m.y, (uint32_t)(ny - 1), by, c.fy);
+  lattice(m.z, (uint32_t)(nz - 1), bz, c.fz);
   const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
   const float* p = vol + bz * sz + by * sy + bx;
-  const float v000 = __ldg(p), v100 = __ldg(p + 1), v010 = __ldg(p + sy), v110 = __ldg(p + sy + 1);
-  const float v001 = __ldg(p + sz), v101 = __ldg(p + sz + 1), v011 = __ldg(p + sz + sy),
-              v111 = __ldg(p + sz + sy + 1);
-  const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
-  return gz * (gy * (gx * v000 + fx * v100) + fy * (gx * v010 + fx * v110)) +
-         fz * (gy * (gx * v001 + fx * v101) + fy * (gx * v011 + fx * v111));
+  c.v[0] = __ldg(p);
+  c.v[1] = __ldg(p + 1);
+  c.v[2] = __ldg(p + sy);
+  c.v[3] = __ldg(p + sy + 1);
+  c.v[4] = __ldg(p + sz);
+  c.v[5] = __ldg(p + sz + 1);
+  c.v[6] = __ldg(p + sz + sy);
+  c.v[7] = __ldg(p + sz + sy + 1);
+  return c;
+}
+
+__device__ __forceinline__ float vol_interp(const VolCorners& c) {
+  const float gx = 1.f - c.fx, gy = 1.f - c.fy, gz = 1.f - c.fz;
+  return gz * (gy * (gx * c.v[0] + c.fx * c.v[1]) + c.fy * (gx * c.v[2] + c.fx * c.v[3])) +
+         c.fz * (gy * (gx * c.v[4] + c.fx * c.v[5]) + c.fy * (gx * c.v[6] + c.fx * c.v[7]));
+}
+
+__device__ __forceinline__ float volume_trilinear(const float* __restrict__ vol, int nx, int ny,
+                                                  int nz, uint3 m) {
+  return vol_interp(vol_fetch(vol, nx, ny, nz, m));
 }
 
 __device__ __forceinline__ void value_range(const ModelState* st, float& vmin, float& inv_range) {

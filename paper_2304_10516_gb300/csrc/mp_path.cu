@@ -80,6 +80,9 @@ struct MpParams {
   float* dbg_dx0;
   float* dbg_tgt;
   uint32_t* dbg_coords;
+  // per-CTA partial weight gradients and loss, reduced by k_mp_reduce
+  float* partial;
+  int32_t n_mlp, part_stride, slots_per_cta;
 };
 
 struct MpDecodeParams {
@@ -180,65 +183,100 @@ __device__ __forceinline__ void st_row(uint8_t* base, uint32_t off, const float*
 
 // Hash-grid encoding of one coordinate, FP16 tables, FP32 interpolation,
 // written as FP16 to the sample's row of the ACT tile (feature 0 .. D-1).
+// The corner loads of kLevelGroup levels are issued together so that their
+// latencies overlap.
+constexpr int kLevelGroup = 4;
+
 template <int F>
 __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half* __restrict__ tab16,
                                                uint3 m, bool valid, uint8_t* act, uint32_t s) {
-  for (int l = 0; l < lv.L; ++l) {
-    float acc[F];
+  for (int l0 = 0; l0 < lv.L; l0 += kLevelGroup) {
+    float v[kLevelGroup][8][F];
+    float fr[kLevelGroup][3];
 #pragma unroll
-    for (int f = 0; f < F; ++f) acc[f] = 0.f;
-    if (valid) {
-      uint32_t bx, by, bz;
-      float fx, fy, fz;
-      lattice(m.x, lv.N[l], bx, fx);
-      lattice(m.y, lv.N[l], by, fy);
-      lattice(m.z, lv.N[l], bz, fz);
-      const __half* tab = tab16 + lv.off[l];
-      float v[8][F];
-      uint32_t idx[8];
+    for (int g = 0; g < kLevelGroup; ++g) {
+      const int l = l0 + g;
+      const bool on = valid && l < lv.L;
+      uint32_t bx = 0, by = 0, bz = 0;
+      fr[g][0] = fr[g][1] = fr[g][2] = 0.f;
+      if (on) {
+        lattice(m.x, lv.N[l], bx, fr[g][0]);
+        lattice(m.y, lv.N[l], by, fr[g][1]);
+        lattice(m.z, lv.N[l], bz, fr[g][2]);
+      }
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        idx[k] = corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+      for (int k = 0; k < 8; ++k) {
+        if (on) {
+          const uint32_t idx =
+              corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+          HalfVec<F>::load(tab16 + lv.off[l] + (size_t)idx * F, v[g][k]);
+        } else {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) HalfVec<F>::load(tab + (size_t)idx[k] * F, v[k]);
+          for (int f = 0; f < F; ++f) v[g][k][f] = 0.f;
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < kLevelGroup; ++g) {
+      const int l = l0 + g;
+      if (l >= lv.L) break;
+      const float fx = fr[g][0], fy = fr[g][1], fz = fr[g][2];
+      float acc[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) acc[f] = 0.f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
                         (((k >> 2) & 1) ? fz : 1.f - fz);
 #pragma unroll
-        for (int f = 0; f < F; ++f) acc[f] += w * v[k][f];
+        for (int f = 0; f < F; ++f) acc[f] += w * v[g][k][f];
       }
+      st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
     }
-    st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
   }
 }
 
+// Backward of the encoding: dL/d(encoding) is read from TMEM (16 columns
+// at a time, the warp-collective load runs on every lane) and each level's
+// gradient times the trilinear weights is added to its 8 corner entries
+// with vector reductions. Returns true if a non-finite value was seen.
 template <int F>
-__device__ __forceinline__ bool scatter_grad(const LevelTab& lv, float* __restrict__ grad, uint3 m,
-                                             const float* dx0) {
+__device__ __forceinline__ bool scatter_from_tmem(const LevelTab& lv, float* __restrict__ grad,
+                                                  uint3 m, bool valid, uint32_t tl,
+                                                  float* dbg_row, float inv_S) {
   bool bad = false;
-  for (int l = 0; l < lv.L; ++l) {
-    uint32_t bx, by, bz;
-    float fx, fy, fz;
-    lattice(m.x, lv.N[l], bx, fx);
-    lattice(m.y, lv.N[l], by, fy);
-    lattice(m.z, lv.N[l], bz, fz);
-    float* tab = grad + lv.off[l];
-    float d[F];
+  constexpr int LPC = 16 / F;  // levels per 16-column chunk
+  for (int c = 0; c < lv.in_dim; c += 16) {
+    float d[16];
+    umma::ld16(tl + (uint32_t)c, d);
+    umma::ld_wait();
+    if (!valid) continue;
+    if (dbg_row) {
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-      d[f] = dx0[l * F + f];
-      bad |= !isfinite(d[f]);
+      for (int j = 0; j < 16; ++j) dbg_row[c + j] = d[j] * inv_S;
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
-                      (((k >> 2) & 1) ? fz : 1.f - fz);
-      const uint32_t idx = corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
-      float g[F];
+    for (int q = 0; q < LPC; ++q) {
+      const int l = c / F + q;
+      uint32_t bx, by, bz;
+      float fx, fy, fz;
+      lattice(m.x, lv.N[l], bx, fx);
+      lattice(m.y, lv.N[l], by, fy);
+      lattice(m.z, lv.N[l], bz, fz);
+      float* tab = grad + lv.off[l];
 #pragma unroll
-      for (int f = 0; f < F; ++f) g[f] = w * d[f];
-      red_add<F>(tab + (size_t)idx * F, g);
+      for (int f = 0; f < F; ++f) bad |= !isfinite(d[q * F + f]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
+                        (((k >> 2) & 1) ? fz : 1.f - fz);
+        const uint32_t idx =
+            corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+        float g[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) g[f] = w * d[q * F + f];
+        red_add<F>(tab + (size_t)idx * F, g);
+      }
     }
   }
   return bad;
@@ -325,35 +363,47 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     return *abort_flag == 0u;
   };
 
-  // write the accumulated weight gradients of the current model
+  // hand the run's weight gradients and loss of the current model to this
+  // CTA's partial slot (plain stores; k_mp_reduce sums the slots)
+  const int first_model = (int)(g_begin / p.tiles_per_model);
   auto flush = [&]() {
     umma::fence_after_sync();
+    float* part = p.partial +
+                  ((size_t)blockIdx.x * p.slots_per_cta + (size_t)(cur - first_model)) * p.part_stride;
     if (warp * 32 < W) {
       const int r = warp * 32 + lane;  // output row of the layer
       for (int k = 0; k < H; ++k) {
         const int in = k == 0 ? D : W;
-        float* g = md.grad + p.w_off[k];
+        float* g = part + (p.w_off[k] - p.w_off[0]);
         for (int c = 0; c < in; c += 16) {
           float v[16];
           umma::ld16(tl + p.lay.dw_col[k] + c, v);
           umma::ld_wait();
           if (r < W) {
+            float4* dst = reinterpret_cast<float4*>(g + (size_t)r * in + c);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) atomicAdd(g + (size_t)r * in + c + j, v[j]);
+            for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
           }
         }
       }
     }
-    float* gout = md.grad + p.w_off[H];
+    // dW_out and the loss: sum the four warps through shared memory (the
+    // DZ tile is idle here)
+    float* s_red = reinterpret_cast<float*>(s_dz);
     if (W >= 32) {
 #pragma unroll
-      for (int j = 0; j < NOUT; ++j) atomicAdd(gout + NOUT * lane + j, acc_out[j]);
+      for (int j = 0; j < NOUT; ++j) s_red[warp * (W + 1) + NOUT * lane + j] = acc_out[j];
     } else if (!(lane & 1)) {
-      atomicAdd(gout + (lane >> 1), acc_out[0]);
+      s_red[warp * (W + 1) + (lane >> 1)] = acc_out[0];
     }
     float l = loss_acc;
     for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if (lane == 0) atomicAdd(&md.st->loss_sum, l);
+    if (lane == 0) s_red[warp * (W + 1) + W] = l;
+    __syncthreads();
+    if (tid <= W) {
+      const float t = s_red[tid] + s_red[(W + 1) + tid] + s_red[2 * (W + 1) + tid] + s_red[3 * (W + 1) + tid];
+      part[tid < W ? (p.w_off[H] - p.w_off[0]) + tid : (int64_t)p.n_mlp] = t;
+    }
     umma::fence_before_sync();
     __syncthreads();
   };
@@ -379,9 +429,10 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     const int i = tile * kTile + tid;
     const bool valid = i < p.batch;
     const uint3 mc = valid ? draw_sample(sp, (uint32_t)i, iter) : make_uint3(0u, 0u, 0u);
-    const float target =
-        valid ? (volume_trilinear(md.vol, md.nx, md.ny, md.nz, mc) - vmin) * inv_range : 0.f;
+    VolCorners vc{};
+    if (valid) vc = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc);  // in flight during the encode
     encode_to_tile<F>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
+    const float target = valid ? (vol_interp(vc) - vmin) * inv_range : 0.f;
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
@@ -505,7 +556,6 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
 
     // -- backward: layer k maps H_{k-1} -> Z_k with W_{k-1}
     {
-      float dx0[64];
       for (int k = H; k >= 1; --k) {
         const int in = k == 1 ? D : W;
         if (tid == 0) {
@@ -563,28 +613,13 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
           umma::fence_proxy_async();
           umma::fence_before_sync();
           __syncthreads();
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            if (c * 16 < D) {
-              float v[16];
-              umma::ld16(tl + c * 16, v);
-#pragma unroll
-              for (int j = 0; j < 16; ++j) dx0[c * 16 + j] = v[j];
-            }
-          }
-          umma::ld_wait();
-          umma::fence_before_sync();
         }
       }
-      // -- scatter dL/d(encoding) into the table gradients
-      if (valid) {
-        if (scatter_grad<F>(p.lv, md.grad, mc, dx0)) atomicOr(&md.st->overflow, 1u);
-        if (p.dbg_dx0 && cur == 0) {
-          const float inv_S = 1.0f / S;
-          for (int j = 0; j < D; ++j) p.dbg_dx0[(size_t)i * D + j] = dx0[j] * inv_S;
-        }
-      }
+      // -- scatter dL/d(encoding) (still in TMEM columns 0..D-1) into the table gradients
+      float* dbg_row = (p.dbg_dx0 && cur == 0 && valid) ? p.dbg_dx0 + (size_t)i * D : nullptr;
+      if (scatter_from_tmem<F>(p.lv, md.grad, mc, valid, tl, dbg_row, 1.0f / S))
+        atomicOr(&md.st->overflow, 1u);
+      umma::fence_before_sync();
     }
     first_tile = false;
   }
@@ -604,6 +639,31 @@ teardown:
   __syncthreads();
   umma::fence_after_sync();
   if (warp == 0) umma::tmem_dealloc(tmem, p.lay.tmem_cols);
+}
+
+// Sum the per-CTA partial weight gradients (and losses) of every model: CTA
+// c covered tiles [T c / G, T (c+1) / G) of the model-major tile list, and
+// wrote model m into slot m - (its first model). The MLP gradients are zero
+// before this kernel (Adam clears them), so the sum is stored.
+__global__ void k_mp_reduce(const MpModel* __restrict__ models, const float* __restrict__ partial,
+                            int part_stride, int slots, int n_mlp, int64_t w_off0, int64_t tpm,
+                            int64_t T, int64_t G) {
+  const int m = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j > n_mlp) return;
+  const int64_t t0 = (int64_t)m * tpm, t1 = t0 + tpm;
+  int64_t c = (t0 * G) / T;
+  while (c > 0 && (T * c) / G > t0) --c;
+  while (c + 1 < G && (T * (c + 1)) / G <= t0) ++c;
+  float sum = 0.f;
+  for (; c < G && (T * c) / G < t1; ++c) {
+    const int64_t first = ((T * c) / G) / tpm;
+    sum += partial[((size_t)c * slots + (size_t)(m - first)) * part_stride + j];
+  }
+  if (j < n_mlp)
+    models[m].grad[w_off0 + j] = sum;
+  else
+    models[m].st->loss_sum = sum;
 }
 
 // --------------------------------------------------------- decode kernel ---
@@ -925,6 +985,8 @@ struct MpCache {
   int graph_steps = 0;
   MpModel* d_models = nullptr;
   AdamModelPtrs* d_adam = nullptr;
+  float* d_partial = nullptr;
+  size_t partial_cap = 0;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
@@ -933,7 +995,10 @@ struct MpCache {
     if (graph) cudaGraphDestroy(graph);
     if (d_models) cudaFree(d_models);
     if (d_adam) cudaFree(d_adam);
+    if (d_partial) cudaFree(d_partial);
     if (cap) cudaStreamDestroy(cap);
+    d_partial = nullptr;
+    partial_cap = 0;
     exec = nullptr;
     graph = nullptr;
     d_models = nullptr;
@@ -966,6 +1031,8 @@ MpParams base_params(const dvnr_model m, const MpLayout& lay, const dvnr_train_c
   p.key = make_uint2((uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32));
   p.qtab = m->qtab;
   p.inv_batch = 1.0f / (float)cfg->batch;
+  p.n_mlp = (int32_t)m->n_mlp;
+  p.part_stride = (int32_t)((m->n_mlp + 1 + 3) / 4 * 4);  // rows stay 16-byte aligned
   return p;
 }
 
@@ -974,9 +1041,30 @@ int train_grid(const MpParams& p) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(p.total_tiles, cap));
 }
 
-dvnr_status launch_train(const MpParams& p, int W, int F, cudaStream_t s) {
-  ProfScope ps("train_fused_fp16", s);
-  DVNR_WF_DISPATCH(W, F, launch_train_wf, p, train_grid(p), s);
+// Partial slots per CTA: the most models one CTA's contiguous tile run can
+// touch.
+int slots_per_cta(const MpParams& p) {
+  const int64_t G = train_grid(p);
+  const int64_t per = (p.total_tiles + G - 1) / G;
+  return (int)((per + p.tiles_per_model - 1) / p.tiles_per_model + 1);
+}
+
+size_t partial_floats(const MpParams& p) {
+  return (size_t)train_grid(p) * (size_t)slots_per_cta(p) * (size_t)p.part_stride;
+}
+
+dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStream_t s) {
+  {
+    ProfScope ps("train_fused_fp16", s);
+    DVNR_WF_DISPATCH(W, F, launch_train_wf, p, train_grid(p), s);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  {
+    ProfScope ps("mp_reduce", s);
+    dim3 grid((unsigned)((p.n_mlp + 1 + 255) / 256), (unsigned)n_models);
+    k_mp_reduce<<<grid, 256, 0, s>>>(p.models, p.partial, p.part_stride, p.slots_per_cta, p.n_mlp,
+                                     p.w_off[0], p.tiles_per_model, p.total_tiles, train_grid(p));
+  }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;
 }
@@ -1035,10 +1123,23 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   MpParams p = base_params(m0, lay, cfg);
   p.total_tiles = (int64_t)p.tiles_per_model * n;
   p.models = c->d_models;
+  p.slots_per_cta = slots_per_cta(p);
+  const size_t need = partial_floats(p);
+  if (c->partial_cap < need) {
+    if (c->d_partial) {
+      DVNR_CUDA(cudaStreamSynchronize(s));
+      cudaFree(c->d_partial);
+      c->d_partial = nullptr;
+      c->partial_cap = 0;
+    }
+    DVNR_CUDA(cudaMalloc(&c->d_partial, need * sizeof(float)));
+    c->partial_cap = need;
+  }
+  p.partial = c->d_partial;
   const int W = m0->mlp.width, F = m0->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
   auto one_step = [&](cudaStream_t st) -> dvnr_status {
-    dvnr_status rc = launch_train(p, W, F, st);
+    dvnr_status rc = launch_train(p, W, F, n, st);
     if (rc != DVNR_OK) return rc;
     return launch_adam(c->d_adam, n, m0->n_params, h, st);
   };
@@ -1075,7 +1176,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   while (left >= G) {
     DVNR_CUDA(cudaGraphLaunch(c->exec, s));
-    count_launches(2 * G);
+    count_launches(3 * G);  // train, reduce, Adam per step
     left -= G;
   }
   for (int64_t i = 0; i < left; ++i) {
@@ -1110,9 +1211,14 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
   if (!(dbg.y && dbg.target && dbg.coords)) {
     p.dbg_y = nullptr;  // the per-sample outputs are written together
   }
+  p.slots_per_cta = slots_per_cta(p);
+  float* part = nullptr;
+  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&part), partial_floats(p) * sizeof(float), s));
+  p.partial = part;
   const int W = m->mlp.width, F = m->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
-  dvnr_status rc = launch_train(p, W, F, s);
+  dvnr_status rc = launch_train(p, W, F, 1, s);
+  cudaFreeAsync(part, s);
   cudaFreeAsync(d, s);
   DVNR_CUDA(cudaStreamSynchronize(s));  // the host descriptor is released on return
   return rc;
