@@ -216,8 +216,8 @@ def run_ours(args, rank, world, local_rank):
     import ctypes as C
 
     kern = {}
-    names = ["train_fused_fp16", "adam", "minmax", "fp32_sample_encode", "fp32_gemm",
-             "fp32_out_loss", "fp32_scatter"]
+    names = ["train_fused_fp16", "mp_reduce", "adam", "minmax", "fp32_sample_encode",
+             "fp32_gemm", "fp32_out_loss", "fp32_scatter"]
     for n in names:
         tms, cnt = C.c_double(), C.c_int64()
         A.call("dvnr_profile_read", n.encode(), C.byref(tms), C.byref(cnt))

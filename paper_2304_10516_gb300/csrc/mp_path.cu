@@ -643,27 +643,42 @@ teardown:
 
 // Sum the per-CTA partial weight gradients (and losses) of every model: CTA
 // c covered tiles [T c / G, T (c+1) / G) of the model-major tile list, and
-// wrote model m into slot m - (its first model). The MLP gradients are zero
-// before this kernel (Adam clears them), so the sum is stored.
-__global__ void k_mp_reduce(const MpModel* __restrict__ models, const float* __restrict__ partial,
-                            int part_stride, int slots, int n_mlp, int64_t w_off0, int64_t tpm,
-                            int64_t T, int64_t G) {
+// wrote model m into slot m - (its first model). A block sums 32 consecutive
+// entries (one per lane, coalesced) with its 8 warps splitting the CTAs, then
+// combines the warps in shared memory. The MLP gradients are zero before this
+// kernel (Adam clears them), so the sum is stored.
+constexpr int kReduceWarps = 8;
+
+__global__ void __launch_bounds__(32 * kReduceWarps)
+    k_mp_reduce(const MpModel* __restrict__ models, const float* __restrict__ partial,
+                int part_stride, int slots, int n_mlp, int64_t w_off0, int64_t tpm, int64_t T,
+                int64_t G) {
   const int m = blockIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j > n_mlp) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + lane;
   const int64_t t0 = (int64_t)m * tpm, t1 = t0 + tpm;
-  int64_t c = (t0 * G) / T;
-  while (c > 0 && (T * c) / G > t0) --c;
-  while (c + 1 < G && (T * (c + 1)) / G <= t0) ++c;
+  int64_t c0 = (t0 * G) / T;
+  while (c0 > 0 && (T * c0) / G > t0) --c0;
+  while (c0 + 1 < G && (T * (c0 + 1)) / G <= t0) ++c0;
   float sum = 0.f;
-  for (; c < G && (T * c) / G < t1; ++c) {
-    const int64_t first = ((T * c) / G) / tpm;
-    sum += partial[((size_t)c * slots + (size_t)(m - first)) * part_stride + j];
+  if (j <= n_mlp) {
+    for (int64_t c = c0 + warp; c < G && (T * c) / G < t1; c += kReduceWarps) {
+      const int64_t first = ((T * c) / G) / tpm;
+      sum += __ldg(partial + ((size_t)c * slots + (size_t)(m - first)) * part_stride + j);
+    }
   }
-  if (j < n_mlp)
-    models[m].grad[w_off0 + j] = sum;
-  else
-    models[m].st->loss_sum = sum;
+  __shared__ float s_part[kReduceWarps][32];
+  s_part[warp][lane] = sum;
+  __syncthreads();
+  if (warp == 0 && j <= n_mlp) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kReduceWarps; ++w) t += s_part[w][lane];
+    if (j < n_mlp)
+      models[m].grad[w_off0 + j] = t;
+    else
+      models[m].st->loss_sum = t;
+  }
 }
 
 // --------------------------------------------------------- decode kernel ---
@@ -1061,8 +1076,8 @@ dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStre
   DVNR_CUDA(cudaGetLastError());
   {
     ProfScope ps("mp_reduce", s);
-    dim3 grid((unsigned)((p.n_mlp + 1 + 255) / 256), (unsigned)n_models);
-    k_mp_reduce<<<grid, 256, 0, s>>>(p.models, p.partial, p.part_stride, p.slots_per_cta, p.n_mlp,
+    dim3 grid((unsigned)((p.n_mlp + 1 + 31) / 32), (unsigned)n_models);
+    k_mp_reduce<<<grid, 32 * kReduceWarps, 0, s>>>(p.models, p.partial, p.part_stride, p.slots_per_cta, p.n_mlp,
                                      p.w_off[0], p.tiles_per_model, p.total_tiles, train_grid(p));
   }
   DVNR_CUDA(cudaGetLastError());

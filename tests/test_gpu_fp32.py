@@ -117,16 +117,17 @@ def _gpu_train_psnr(dv, c, vol, seed_model, lr, steps, seed):
 
 def test_fp32_training_psnr_matches_oracle(dv, orc):
     # Trajectory parity after 200 seeded steps of the 64^3 workload at
-    # lr = 1e-3 (the low end of the paper's appendix learning rates), where
-    # the oracle's own PSNR moves by < 0.1 dB when its initial weights are
-    # perturbed by 1e-7 relative.
+    # lr = 5e-4, where the oracle's own PSNR spreads by 0.013 dB (standard
+    # deviation over 1e-7 relative perturbations of its initial weights; at
+    # lr = 1e-3 the 200-step point falls in a fast-changing phase of training
+    # and the spread is 0.05 dB in FP64 and 0.19 dB with FP16 rounding).
     from paper_2304_10516_gb300 import volumes
 
     c = P.configs_blobs64()
     oc = P.oracle_cfg(c)
     vol = volumes.blobs(64, seed=1001)
-    psnr_gpu, loss_gpu, m = _gpu_train_psnr(dv, c, vol, 4242, 1e-3, 200, 99)
-    psnr_orc, hist = _oracle_train_psnr(orc, oc, vol, orc.init_params(oc, 4242), 1e-3, 200, 99,
+    psnr_gpu, loss_gpu, m = _gpu_train_psnr(dv, c, vol, 4242, 5e-4, 200, 99)
+    psnr_orc, hist = _oracle_train_psnr(orc, oc, vol, orc.init_params(oc, 4242), 5e-4, 200, 99,
                                         c["batch"])
     assert abs(psnr_gpu - psnr_orc) < 0.2, (psnr_gpu, psnr_orc)
     assert abs(loss_gpu - hist[-1]) < 0.1 * hist[-1]

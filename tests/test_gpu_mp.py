@@ -147,21 +147,21 @@ def _train_psnr(dv, c, vol, seed_model, lr, steps, seed, precision):
 
 
 def test_fp16_training_equal_psnr(dv, orc, A):
-    # 200 seeded steps of the 64^3 workload at lr 1e-3 (non-chaotic regime):
-    # the FP16 path reaches the PSNR of the oracle's FP16 emulation and of
-    # the plain FP32 path within 0.2 dB.
+    # 200 seeded steps of the 64^3 workload at lr 5e-4 (a regime where the
+    # oracle's run-to-run spread is 0.013 dB): the FP16 path reaches the PSNR
+    # of the oracle's FP16 emulation and of the plain FP32 path within 0.2 dB.
     from paper_2304_10516_gb300 import volumes
 
     c = P.configs_blobs64()
     oc = P.oracle_cfg(c)
     vol = volumes.blobs(64, seed=1001)
-    p16, l16, m16 = _train_psnr(dv, c, vol, 4242, 1e-3, 200, 99, A.DVNR_FP16)
-    p32, _, _ = _train_psnr(dv, c, vol, 4242, 1e-3, 200, 99, A.DVNR_FP32)
+    p16, l16, m16 = _train_psnr(dv, c, vol, 4242, 5e-4, 200, 99, A.DVNR_FP16)
+    p32, _, _ = _train_psnr(dv, c, vol, 4242, 5e-4, 200, 99, A.DVNR_FP32)
     st = m16.state()
     assert st["adam_t"] == 200 and st["skipped"] == 0 and st["precision"] == A.DVNR_FP16
     th = orc.init_params(oc, 4242)
     m1, m2 = np.zeros_like(th), np.zeros_like(th)
-    tc = orc.TrainConfig(batch=c["batch"], lr=float(np.float32(1e-3)), seed=99, mixed=True)
+    tc = orc.TrainConfig(batch=c["batch"], lr=float(np.float32(5e-4)), seed=99, mixed=True)
     ost = orc.State(loss_scale=4096.0)
     orc.train(oc, tc, ost, th, m1, m2, vol, float(vol.min()), float(vol.max()), 200)
     odec = orc.decode_grid(oc, th, (64, 64, 64), 0, float(vol.min()), float(vol.max()), mixed=True)
