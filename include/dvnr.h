@@ -248,6 +248,28 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf,
 dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n,
                              double* out_host, void* stream);
 
+/* Allocation-free variant of dvnr_error_stats (the paper has no counterpart;
+ * this call exists for library users). For callers that must not allocate
+ * device memory when they ask for the error: an in situ pipeline whose
+ * simulation has reserved the device memory for itself, or a time step that
+ * must not pay the implicit device synchronisation of cudaMalloc/cudaFree.
+ * Same results as dvnr_error_stats (up to the order of the FP64 additions):
+ * out_host[0] = sum of squared differences, out_host[1] = max |a - b|.
+ *  - Scratch: a fixed device array inside the library (64 KiB + 16 B per
+ *    GPU that loads the library, held until the process exits); the call
+ *    allocates nothing.
+ *  - Limit: n <= 2^28 (268435456) elements; larger n returns DVNR_E_INVALID
+ *    with a message, before any device work.
+ *  - The first call on a device looks up the scratch address on that device
+ *    (the device must be current); make that first call before any stream
+ *    capture.
+ *  - All calls share the scratch array and leave their partial sums in it;
+ *    calls whose kernels overlap on the GPU (e.g. on two streams) race and
+ *    must be serialised by the caller.
+ *  - Synchronises `stream`.                                                 */
+dvnr_status dvnr_error_stats_noalloc(const float* a_dev, const float* b_dev, int64_t n,
+                                     double* out_host, void* stream);
+
 /* Table indices of the 8 cell corners per level for n fixed-point
  * coordinates (the indices the training and decoding kernels gather):
  * idx_dev is n x n_levels x 8, corner k = (k&1, (k>>1)&1, (k>>2)&1).       */

@@ -28,6 +28,7 @@ EXPORTS = [
     "dvnr_get_state", "dvnr_train", "dvnr_train_grad", "dvnr_decode_points", "dvnr_decode_grid",
     "dvnr_render", "dvnr_error_stats", "dvnr_corner_indices", "dvnr_profile_enable",
     "dvnr_profile_read", "dvnr_launch_count", "dvnr_selftest_umma",
+    "dvnr_error_stats_noalloc",
 ]
 
 
@@ -100,6 +101,7 @@ _SIGS = {
     "dvnr_profile_read": ([C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "dvnr_launch_count": ([], C.c_int64),
     "dvnr_selftest_umma": ([_P], C.c_int),
+    "dvnr_error_stats_noalloc": ([_P, _P, C.c_int64, _P, _P], C.c_int),
 }
 
 

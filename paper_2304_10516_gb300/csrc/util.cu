@@ -1,6 +1,7 @@
 // util.cu -- initialisation, value-range pre-pass, fused Adam, FP64 error
 // reduction and the corner-index probe of libdvnr.
 #include <cstring>
+#include <mutex>
 
 #include "dvnr_internal.cuh"
 
@@ -387,3 +388,154 @@ dvnr_status launch_adam(const AdamModelPtrs* models_dev, int n_models, int64_t n
 }
 
 }  // namespace dvnr
+
+// ---------------------------------------------------------------------------
+// Allocation-free FP64 error statistics.
+//
+// For callers that must not allocate device memory when they ask for the
+// error -- for example an in situ pipeline whose simulation has reserved the
+// device memory for itself, or a time step that must not pay the implicit
+// device synchronisation of cudaMalloc/cudaFree. The scratch lives in a
+// fixed file-scope device array: one (sum, max) pair per block of
+// kErrChunk elements, plus the final pair. Every GPU that loads the
+// library holds it (64 KiB + 16 B) until the process exits.
+namespace dvnr {
+namespace {
+constexpr int kErrBlocksMax = 4096;            // partial pairs in the scratch array
+constexpr int64_t kErrChunk = 1 << 16;         // elements reduced by one block
+constexpr int64_t kErrMaxN = (int64_t)kErrBlocksMax * kErrChunk;  // 2^28 elements
+}  // namespace
+}  // namespace dvnr
+
+static __device__ __align__(256) double g_err_scratch[2 * dvnr::kErrBlocksMax + 2];
+
+namespace dvnr {
+namespace {
+
+// Block b reduces elements [b kErrChunk, (b+1) kErrChunk) into part[2b],
+// part[2b+1]; every pair of the launch is overwritten, so nothing has to be
+// cleared between calls.
+__global__ void __launch_bounds__(kThreads) k_error_partials(const float* __restrict__ a,
+                                                            const float* __restrict__ b,
+                                                            int64_t n, double* part) {
+  const int64_t lo = (int64_t)blockIdx.x * kErrChunk;
+  const int64_t hi = lo + kErrChunk < n ? lo + kErrChunk : n;
+  double s = 0.0, mx = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double d = (double)__ldg(a + i) - (double)__ldg(b + i);
+    s += d * d;
+    mx = fmax(mx, fabs(d));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __shared__ double ss[kThreads / 32], sm[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    ss[threadIdx.x >> 5] = s;
+    sm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, m = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      t += ss[w];
+      m = fmax(m, sm[w]);
+    }
+    part[2 * blockIdx.x] = t;
+    part[2 * blockIdx.x + 1] = m;
+  }
+}
+
+// One block folds the nb partial pairs (fixed order) into out[0], out[1].
+__global__ void __launch_bounds__(kThreads) k_error_final(double* part, int nb, double* out) {
+  double s = 0.0, mx = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    s += part[2 * i];
+    mx = fmax(mx, part[2 * i + 1]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __shared__ double ss[kThreads / 32], sm[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) {
+    ss[threadIdx.x >> 5] = s;
+    sm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, m = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) {
+      t += ss[w];
+      m = fmax(m, sm[w]);
+    }
+    out[0] = t;
+    out[1] = m;
+  }
+}
+
+// Device address of g_err_scratch per device, looked up once per device
+// (with that device current) on its first call.
+constexpr int kMaxDevices = 64;
+double* g_err_scratch_ptr[kMaxDevices] = {};
+std::mutex g_err_scratch_mu;
+
+dvnr_status err_scratch(double** out) {
+  int dev = 0;
+  DVNR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("device ordinal %d beyond the %d devices this call supports", dev, kMaxDevices);
+    return DVNR_E_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_err_scratch_mu);
+  if (!g_err_scratch_ptr[dev]) {
+    void* p = nullptr;
+    DVNR_CUDA(cudaGetSymbolAddress(&p, g_err_scratch));
+    g_err_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_err_scratch_ptr[dev];
+  return DVNR_OK;
+}
+
+}  // namespace
+}  // namespace dvnr
+
+extern "C" dvnr_status dvnr_error_stats_noalloc(const float* a_dev, const float* b_dev, int64_t n,
+                                                double* out_host, void* stream) {
+  using namespace dvnr;
+  if (!out_host || n < 0 || (n > 0 && (!a_dev || !b_dev))) {
+    set_error("bad argument");
+    return DVNR_E_INVALID;
+  }
+  if (n > kErrMaxN) {
+    set_error("n = %lld exceeds the %lld elements the static scratch of dvnr_error_stats_noalloc "
+              "can reduce",
+              (long long)n, (long long)kErrMaxN);
+    return DVNR_E_INVALID;
+  }
+  if (n == 0) {
+    out_host[0] = 0.0;
+    out_host[1] = 0.0;
+    return DVNR_OK;
+  }
+  double* scratch = nullptr;
+  dvnr_status rc = err_scratch(&scratch);
+  if (rc != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nb = (int)((n + kErrChunk - 1) / kErrChunk);
+  double* fin = scratch + 2 * kErrBlocksMax;
+  {
+    ProfScope ps("error_stats_noalloc", s);
+    k_error_partials<<<nb, kThreads, 0, s>>>(a_dev, b_dev, n, scratch);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  {
+    ProfScope ps("error_stats_noalloc", s);
+    k_error_final<<<1, kThreads, 0, s>>>(scratch, nb, fin);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  DVNR_CUDA(cudaMemcpyAsync(out_host, fin, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  DVNR_CUDA(cudaStreamSynchronize(s));
+  return DVNR_OK;
+}
