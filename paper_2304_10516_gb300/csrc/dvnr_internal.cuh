@@ -226,14 +226,16 @@ __device__ __forceinline__ VolCorners vol_fetch(const float* __restrict__ vol, i
   lattice(m.z, (uint32_t)(nz - 1), bz, c.fz);
   const size_t sy = (size_t)nx, sz = (size_t)nx * ny;
   const float* p = vol + bz * sz + by * sy + bx;
-  c.v[0] = __ldg(p);
-  c.v[1] = __ldg(p + 1);
-  c.v[2] = __ldg(p + sy);
-  c.v[3] = __ldg(p + sy + 1);
-  c.v[4] = __ldg(p + sz);
-  c.v[5] = __ldg(p + sz + 1);
-  c.v[6] = __ldg(p + sz + sy);
-  c.v[7] = __ldg(p + sz + sy + 1);
+  // evict-first: a training volume is read at eight random corners per sample
+  // and is larger than the share of L2 the tables and gradients need
+  c.v[0] = __ldcs(p);
+  c.v[1] = __ldcs(p + 1);
+  c.v[2] = __ldcs(p + sy);
+  c.v[3] = __ldcs(p + sy + 1);
+  c.v[4] = __ldcs(p + sz);
+  c.v[5] = __ldcs(p + sz + 1);
+  c.v[6] = __ldcs(p + sz + sy);
+  c.v[7] = __ldcs(p + sz + sy + 1);
   return c;
 }
 

@@ -656,15 +656,19 @@ __global__ void __launch_bounds__(32 * kReduceWarps)
   const int m = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
-  const int64_t t0 = (int64_t)m * tpm, t1 = t0 + tpm;
-  int64_t c0 = (t0 * G) / T;
-  while (c0 > 0 && (T * c0) / G > t0) --c0;
-  while (c0 + 1 < G && (T * (c0 + 1)) / G <= t0) ++c0;
+  // tile counts stay below 2^31 / G, so 32-bit products and quotients suffice
+  const uint32_t T32 = (uint32_t)T, G32 = (uint32_t)G, tpm32 = (uint32_t)tpm;
+  const uint32_t t0 = (uint32_t)m * tpm32, t1 = t0 + tpm32;
+  uint32_t c0 = (uint32_t)(((uint64_t)t0 * G32) / T32);
+  while (c0 > 0 && (T32 * c0) / G32 > t0) --c0;
+  while (c0 + 1 < G32 && (T32 * (c0 + 1)) / G32 <= t0) ++c0;
   float sum = 0.f;
   if (j <= n_mlp) {
-    for (int64_t c = c0 + warp; c < G && (T * c) / G < t1; c += kReduceWarps) {
-      const int64_t first = ((T * c) / G) / tpm;
-      sum += __ldg(partial + ((size_t)c * slots + (size_t)(m - first)) * part_stride + j);
+    for (uint32_t c = c0 + warp; c < G32; c += kReduceWarps) {
+      const uint32_t begin = (T32 * c) / G32;
+      if (begin >= t1) break;
+      const uint32_t first = begin / tpm32;
+      sum += __ldg(partial + ((size_t)c * slots + (m - first)) * part_stride + j);
     }
   }
   __shared__ float s_part[kReduceWarps][32];
@@ -1137,6 +1141,10 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   MpParams p = base_params(m0, lay, cfg);
   p.total_tiles = (int64_t)p.tiles_per_model * n;
+  if (p.total_tiles * (int64_t)train_grid(p) >= (1LL << 32)) {
+    set_error("FP16 path: %lld tiles per step is beyond the supported range", (long long)p.total_tiles);
+    return DVNR_E_UNSUPPORTED;
+  }
   p.models = c->d_models;
   p.slots_per_cta = slots_per_cta(p);
   const size_t need = partial_floats(p);

@@ -169,7 +169,10 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
     float4* m14 = reinterpret_cast<float4*>(md.m1);
     float4* m24 = reinterpret_cast<float4*>(md.m2);
     for (int64_t i = tid; i < n4; i += stride) {
-      float4 g = g4[i], th = th4[i], a = m14[i], b = m24[i];
+      // streaming loads/stores (evict-first): this pass touches every optimiser
+      // word once per step and would otherwise push the tables, the FP16 copy
+      // and the gradients that the next step gathers out of L2
+      float4 g = __ldcs(g4 + i), th = __ldcs(th4 + i), a = __ldcs(m14 + i), b = __ldcs(m24 + i);
       float* gp = &g.x;
       float* tp = &th.x;
       float* ap = &a.x;
@@ -181,9 +184,9 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
         bp[j] = h.beta2 * bp[j] + ib2 * gg * gg;
         tp[j] -= h.lr * (ap[j] / bc1) / (sqrtf(bp[j] / bc2) + h.eps);
       }
-      th4[i] = th;
-      m14[i] = a;
-      m24[i] = b;
+      __stcs(th4 + i, th);
+      __stcs(m14 + i, a);
+      __stcs(m24 + i, b);
       g4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       __half2* h2 = reinterpret_cast<__half2*>(md.theta16) + 2 * i;
       h2[0] = __floats2half2_rn(th.x, th.y);
