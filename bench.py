@@ -42,6 +42,16 @@ WORKLOADS = {
                              "MLP 32-64-64-64-1, batch 2^18",
                         shape=(256, 256, 256), seed=1002, L=16, F=2, log2T=19, base=16, growth=1.38,
                         width=64, hidden=3, batch=1 << 18, steps_full=2000, lam=0.0, lr=1e-2),
+    "blocks64": dict(desc="1024x1024x512 spectral field, 64 uneven blocks (4x4x4 over [0,512)^3, edges "
+                          "96-160, 1 ghost layer), one INR each (L=16 F=2 T=2^17 N0=16 b=1.38, MLP "
+                          "32-64-64-64-1), 2^14 samples/model/step, lambda 0.15",
+                     shape=(512, 1024, 1024), seed=1004, L=16, F=2, log2T=17, base=16, growth=1.38,
+                     width=64, hidden=3, batch=1 << 14, steps_full=2000, lam=0.15, lr=1e-2),
+    "insitu512": dict(desc="16 advected 512^3 spectral steps, warm start, 500 iterations each, "
+                           "decode 512^3, ray-march 1024x1024x512 (L=16 F=2 T=2^19, MLP 32-64-64-64-1, "
+                           "batch 2^18, lambda 0.15)",
+                      shape=(512, 512, 512), seed=1005, L=16, F=2, log2T=19, base=16, growth=1.38,
+                      width=64, hidden=3, batch=1 << 18, steps_full=500, lam=0.15, lr=1e-2, t_steps=16),
     "blobs64": dict(desc="64^3 Gaussian blobs, L=8 F=2 T=2^15 N0=4 b=1.5, MLP 16-32-32-1, batch 4096",
                     shape=(64, 64, 64), seed=1001, L=8, F=2, log2T=15, base=4, growth=1.5,
                     width=32, hidden=2, batch=4096, steps_full=200, lam=0.0, lr=1e-2),
@@ -310,6 +320,223 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+def _profile(A, names):
+    import ctypes as C
+
+    out = {}
+    for n in names:
+        tms, cnt = C.c_double(), C.c_int64()
+        A.call("dvnr_profile_read", n.encode(), C.byref(tms), C.byref(cnt))
+        if cnt.value:
+            out[n] = (tms.value, cnt.value)
+    return out
+
+
+def _roofline(kern, w, n_params, units, hbm_peak, have_peaks):
+    total = sum(v[0] for v in kern.values())
+    dom = max(kern, key=lambda k: kern[k][0])
+    dms, dcnt = kern[dom]
+    byt = kernel_bytes(dom, w, n_params, units)
+    ach = byt / (dms / dcnt / 1e3) / 1e9 if byt else None
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+            "frac": (ach / hbm_peak) if ach else None, "traffic": None,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if have_peaks else "fallback",
+            "avg_launch_ms": dms / dcnt,
+            "share": {k: round(v[0] / total, 4) for k, v in kern.items()}}
+
+
+def _peaks():
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(p.get("hbm_gbs", 6800.0)), True
+    except Exception:
+        return 6800.0, False
+
+
+def run_blocks(args, rank, world, local_rank):
+    """The partitioned workload: 64 uneven blocks of a 1024x1024x512 field,
+    one INR each, all trained by one grouped launch per step."""
+    import torch
+
+    from paper_2304_10516_gb300 import _abi as A
+    from paper_2304_10516_gb300 import model as dv
+    from paper_2304_10516_gb300 import volumes
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOADS["blocks64"]
+    lib = A.load()
+    field = volumes.spectral_torch(w["shape"], seed=w["seed"] + rank, device=dev)
+    boxes = volumes.uneven_boxes((512, 512, 512), (4, 4, 4), (96, 160), seed=w["seed"])
+    vols = [volumes.extract_block(field, lo, hi, 1) for lo, hi in boxes]
+    enc = dv.EncodingConfig(w["L"], w["F"], w["log2T"], w["base"], w["growth"])
+    mlp = dv.MLPConfig(w["width"], w["hidden"])
+    models = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
+    n = len(models)
+
+    def cfg(steps, prec=A.DVNR_FP16):
+        return dv.TrainConfig(batch=w["batch"], steps=steps, lr=w["lr"], lambda_bnd=w["lam"],
+                              sigma_bnd=0.005, precision=prec, seed=7 + rank)
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0 if "CUDA_VISIBLE_DEVICES" in os.environ else local_rank)
+    dv.train(models, vols, cfg(max(args.warmup, 3)))
+    torch.cuda.synchronize()
+    l0 = lib.dvnr_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dv.train(models, vols, cfg(args.steps), sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = lib.dvnr_launch_count() - l0
+    clk = clocks.stop()
+    samples = n * w["batch"] * args.steps * world
+    res = {
+        "metric": "INR train samples/s and decode samples/s at equal PSNR vs plain FP32 path",
+        "value": samples / (ms / 1e3), "unit": "train samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic (seeded random-phase k^-5/3 spectral field)",
+        "config": {"workload": w["desc"], "models": n, "global_batch": n * w["batch"] * world,
+                   "parallelism": "64 independent partition models in one grouped launch per GPU",
+                   "l2": "working set > L2 (no flush needed)"},
+        "clocks": clk, "gpu_launches": int(launches)}
+    if rank != 0 or args.no_extras:
+        return res
+    hbm, have = _peaks()
+    A.call("dvnr_profile_enable", 1)
+    dv.train(models, vols, cfg(min(args.steps, 20)))
+    kern = _profile(A, ["train_fused_fp16", "mp_reduce", "adam", "minmax"])
+    A.call("dvnr_profile_enable", 0)
+    res["roofline"] = _roofline(kern, w, models[0].n_params * n, n * w["batch"], hbm, have)
+    # full training from fresh models, then decode and PSNR over owned voxels
+    for i, m in enumerate(models):
+        m.close()
+    models = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
+    t0 = time.perf_counter()
+    dv.train(models, vols, cfg(w["steps_full"]))
+    t_full = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    grids = [torch.empty(tuple(h - l for l, h in zip(lo, hi))[::-1], device=dev) for lo, hi in boxes]
+    d0.record(stream)
+    for m, g in zip(models, grids):
+        m.decode_grid(g)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dec_ms = d0.elapsed_time(d1)
+    sse, vox = 0.0, 0
+    for (lo, hi), g in zip(boxes, grids):
+        ref = field[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].contiguous()
+        s_, _ = dv.error_stats(g, ref)
+        sse += s_
+        vox += g.numel()
+    psnr = 10 * math.log10(1.0 / (sse / vox))
+    res["decode"] = {"value": vox / (dec_ms / 1e3), "unit": "decode samples/s", "ms": dec_ms,
+                     "points": vox}
+    res["psnr"] = {"path": psnr, "steps": w["steps_full"], "voxel_weighted": True}
+    res["e2e"] = {"value": n * w["batch"] * w["steps_full"] / t_full, "unit": "train samples/s",
+                  "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * n,
+                  "step": f"{w['steps_full']} grouped iterations of all 64 models, read losses"}
+    # plain FP32 path on the same blocks (one model after another), throughput only
+    f32 = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
+    dv.train(f32, vols, cfg(3, A.DVNR_FP32))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dv.train(f32, vols, cfg(20, A.DVNR_FP32))
+    t32 = time.perf_counter() - t0
+    res["fp32_path"] = {"value": n * w["batch"] * 20 / t32, "unit": "train samples/s",
+                        "speedup": (n * w["batch"] * 20 / t32) and res["value"] / (n * w["batch"] * 20 / t32)}
+    res["cpu_baseline"] = cpu_baseline(w, vols[0].cpu().numpy())
+    return res
+
+
+def run_insitu(args, rank, world, local_rank):
+    """In situ time series: each step of an advected 512^3 field is compressed
+    by an INR warm-started from the previous step's weights (Sec. 3.5),
+    decoded back to the grid and ray-marched."""
+    import torch
+
+    from paper_2304_10516_gb300 import _abi as A
+    from paper_2304_10516_gb300 import model as dv
+    from paper_2304_10516_gb300 import volumes
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = WORKLOADS["insitu512"]
+    lib = A.load()
+    enc = dv.EncodingConfig(w["L"], w["F"], w["log2T"], w["base"], w["growth"])
+    mlp = dv.MLPConfig(w["width"], w["hidden"])
+    n3 = w["shape"][0]
+    tf = dv.make_tf(alpha_max=0.05)
+    clocks = ClockSampler(0 if "CUDA_VISIBLE_DEVICES" in os.environ else local_rank)
+    stream = torch.cuda.current_stream()
+
+    def cfg(steps):
+        return dv.TrainConfig(batch=w["batch"], steps=steps, lr=w["lr"], lambda_bnd=w["lam"],
+                              sigma_bnd=0.005, precision=A.DVNR_FP16, seed=7 + rank)
+
+    # warm-up of the code paths on a throw-away model
+    warm = dv.Model((0, 0, 0), (n3, n3, n3), 0, enc, mlp, seed=1)
+    f0 = volumes.advected_torch(w["shape"], w["seed"] + rank, 0.0, device=dev)
+    dv.train([warm], [f0], cfg(max(args.warmup, 3)))
+    warm.close()
+    grid = torch.empty((n3, n3, n3), device=dev)
+    img = torch.empty((1024, 1024, 4), device=dev)
+    prev = None
+    per = []
+    l0 = lib.dvnr_launch_count()
+    t_train = t_dec = t_ren = 0.0
+    for t in range(w["t_steps"]):
+        field = volumes.advected_torch(w["shape"], w["seed"] + rank, float(t), device=dev)
+        m = dv.Model((0, 0, 0), (n3, n3, n3), 0, enc, mlp, seed=100)
+        if prev is not None:
+            m.copy_weights_from(prev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        dv.train([m], [field], cfg(w["steps_full"]), sync=False)
+        ev[1].record(stream)
+        m.decode_grid(grid)
+        ev[2].record(stream)
+        dv.render([m], tf, 1024, 1024, 512, out=img)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        tr, de, re_ = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+        t_train += tr
+        t_dec += de
+        t_ren += re_
+        sse, _ = dv.error_stats(grid, field)
+        per.append({"t": t, "train_ms": tr, "decode_ms": de, "render_ms": re_,
+                    "psnr": 10 * math.log10(1.0 / (sse / grid.numel())),
+                    "last_loss": m.state()["last_loss"]})
+        if prev is not None:
+            prev.close()
+        prev = m
+        del field
+    launches = lib.dvnr_launch_count() - l0
+    clk = clocks.stop()
+    T = w["t_steps"]
+    samples = T * w["steps_full"] * w["batch"] * world
+    res = {
+        "metric": "INR train samples/s and decode samples/s at equal PSNR vs plain FP32 path",
+        "value": samples / (t_train / 1e3), "unit": "train samples/s", "n_gpus": world,
+        "steps": T * w["steps_full"], "warmup": args.warmup,
+        "ms_per_step": t_train / (T * w["steps_full"]), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic (seeded advected k^-5/3 spectral field)",
+        "config": {"workload": w["desc"], "global_batch": w["batch"] * world,
+                   "parallelism": "one model per GPU"},
+        "clocks": clk, "gpu_launches": int(launches),
+        "decode": {"value": T * n3 ** 3 / (t_dec / 1e3), "unit": "decode samples/s",
+                   "ms_per_step": t_dec / T},
+        "render": {"value": T * 1024 * 1024 * 512 / (t_ren / 1e3), "unit": "ray samples/s",
+                   "ms_per_step_incl_decode": t_ren / T},
+        "per_step": per,
+    }
+    return res
+
+
 def cpu_baseline(w, vol_np, budget_s=12.0):
     import oracle as orc
 
@@ -387,7 +614,12 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    res = run_ours(args, rank, world, local_rank)
+    if args.workload == "blocks64":
+        res = run_blocks(args, rank, world, local_rank)
+    elif args.workload == "insitu512":
+        res = run_insitu(args, rank, world, local_rank)
+    else:
+        res = run_ours(args, rank, world, local_rank)
     if rank == 0 and res is not None:
         print(json.dumps(res))
     if world > 1:

@@ -312,8 +312,11 @@ static void level_corners(const orc_cfg* c, int l, const uint32_t m[3],
   }
 }
 
-void orc_encode(const orc_cfg* c, const double* theta, const uint32_t m[3],
-                int mixed, double* x0) {
+/* round_params: round each table value to binary16 when it is read;
+ * round_acts: round the interpolated feature to binary16. The public entry
+ * rounds both in mixed mode; the batch paths pre-round the parameters once. */
+static void encode_impl(const orc_cfg* c, const double* theta, const uint32_t m[3],
+                        int round_params, int round_acts, double* x0) {
   for (int l = 0; l < c->L; ++l) {
     corner_set cs;
     level_corners(c, l, m, &cs);
@@ -321,20 +324,43 @@ void orc_encode(const orc_cfg* c, const double* theta, const uint32_t m[3],
       double acc = 0.0;
       for (int k = 0; k < 8; ++k) {
         double v = theta[c->offset[l] + (int64_t)cs.idx[k] * c->F + f];
-        if (mixed) v = orc_round_half(v);
+        if (round_params) v = orc_round_half(v);
         acc += cs.w[k] * v;
       }
-      x0[l * c->F + f] = mixed ? orc_round_half(acc) : acc;
+      x0[l * c->F + f] = round_acts ? orc_round_half(acc) : acc;
     }
   }
 }
 
-void orc_encode_batch(const orc_cfg* c, const double* theta, int64_t n,
-                      const uint32_t* m, int mixed, double* x0) {
+void orc_encode(const orc_cfg* c, const double* theta, const uint32_t m[3],
+                int mixed, double* x0) {
+  encode_impl(c, theta, m, mixed, mixed, x0);
+}
+
+/* Parameters as the mixed-precision path stores them: every value rounded to
+ * binary16 once (returns theta itself when not mixed; free with
+ * release_params). */
+static const double* prepare_params(const orc_cfg* c, const double* theta, int mixed) {
+  if (!mixed) return theta;
+  double* r = (double*)malloc(sizeof(double) * (size_t)c->n_params);
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static)
 #endif
-  for (int64_t i = 0; i < n; ++i) orc_encode(c, theta, m + 3 * i, mixed, x0 + i * c->in_dim);
+  for (int64_t i = 0; i < c->n_params; ++i) r[i] = orc_round_half(theta[i]);
+  return r;
+}
+static void release_params(const double* prepared, const double* theta) {
+  if (prepared != theta) free((void*)prepared);
+}
+
+void orc_encode_batch(const orc_cfg* c, const double* theta, int64_t n,
+                      const uint32_t* m, int mixed, double* x0) {
+  const double* th = prepare_params(c, theta, mixed);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (int64_t i = 0; i < n; ++i) encode_impl(c, th, m + 3 * i, 0, mixed, x0 + i * c->in_dim);
+  release_params(th, theta);
 }
 
 /* Normalised targets (v - min)/(max - min) at n fixed-point coordinates
@@ -394,8 +420,8 @@ static double sample_fwd_bwd(const orc_cfg* c, const double* theta,
   double* z = s->z;
 #define HROW(k) (h + (int64_t)(k) * maxw)
 #define ZROW(k) (z + (int64_t)(k) * W)
-#define WGT(v) (mixed ? orc_round_half(v) : (v))
-  orc_encode(c, theta, m, mixed, HROW(0));
+#define WGT(v) (v) /* parameters arrive pre-rounded in mixed mode */
+  encode_impl(c, theta, m, 0, mixed, HROW(0));
   double mg = INFINITY;
   for (int k = 0; k < H; ++k) {
     const int in = k == 0 ? D : W;
@@ -490,6 +516,7 @@ double orc_fwd_bwd(const orc_cfg* c, const double* theta, int64_t n,
   double* gpart = NULL;
   if (grad_mlp) gpart = (double*)calloc((size_t)nt * c->n_mlp, sizeof(double));
   double loss_sum = 0.0;
+  const double* th = prepare_params(c, theta, mixed);
 #ifdef _OPENMP
 #pragma omp parallel reduction(+ : loss_sum)
 #endif
@@ -509,13 +536,14 @@ double orc_fwd_bwd(const orc_cfg* c, const double* theta, int64_t n,
 #endif
     for (int64_t i = 0; i < n; ++i) {
       loss_sum += sample_fwd_bwd(
-          c, theta, m + 3 * i, target[i], loss, mixed, loss_scale, inv_B,
+          c, th, m + 3 * i, target[i], loss, mixed, loss_scale, inv_B,
           flip ? flip + i * nunits : NULL, gmine, dx0_all + i * D,
           y_out ? y_out + i : NULL, margin_out ? margin_out + i : NULL,
           zabs_out ? zabs_out + i * nunits : NULL, &s);
     }
     free(s.h); free(s.z); free(s.dz); free(s.dh);
   }
+  release_params(th, theta);
   if (grad_mlp) {
     for (int t = 0; t < nt; ++t)
       for (int64_t p = 0; p < c->n_mlp; ++p) grad_mlp[p] += gpart[(int64_t)t * c->n_mlp + p];
@@ -622,6 +650,7 @@ double orc_train(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
 void orc_decode_unit(const orc_cfg* c, const double* theta, int64_t n,
                      const uint32_t* m, int mixed, double vmin, double vmax,
                      double* out) {
+  const double* th = prepare_params(c, theta, mixed);
 #ifdef _OPENMP
 #pragma omp parallel
 #endif
@@ -634,28 +663,29 @@ void orc_decode_unit(const orc_cfg* c, const double* theta, int64_t n,
 #pragma omp for schedule(static)
 #endif
     for (int64_t s = 0; s < n; ++s) {
-      orc_encode(c, theta, m + 3 * s, mixed, a);
+      encode_impl(c, th, m + 3 * s, 0, mixed, a);
       for (int k = 0; k < H; ++k) {
         const int in = k == 0 ? D : W;
-        const double* Wk = theta + c->w_off[k];
+        const double* Wk = th + c->w_off[k];
         for (int j = 0; j < W; ++j) {
           double acc = 0.0;
           for (int i = 0; i < in; ++i) {
             double w = Wk[(int64_t)j * in + i];
-            acc += (mixed ? orc_round_half(w) : w) * a[i];
+            acc += w * a[i];
           }
           double r = acc > 0.0 ? acc : 0.0;
           b[j] = mixed ? orc_round_half(r) : r;
         }
         double* t = a; a = b; b = t;
       }
-      const double* wout = theta + c->w_off[H];
+      const double* wout = th + c->w_off[H];
       double y = 0.0;
-      for (int j = 0; j < W; ++j) y += (mixed ? orc_round_half(wout[j]) : wout[j]) * a[j];
+      for (int j = 0; j < W; ++j) y += wout[j] * a[j];
       out[s] = y * (vmax - vmin) + vmin;
     }
     free(a); free(b);
   }
+  release_params(th, theta);
 }
 
 /* Stored voxel j of n -> fixed-point coordinate round(j 2^24 / (n - 1)),

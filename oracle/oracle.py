@@ -221,14 +221,14 @@ def encode(cfg: Config, theta, m, mixed=False):
 
 
 def fwd_bwd(cfg: Config, theta, m, target, loss=0, mixed=False, loss_scale=1.0,
-            grad_norm_count=None, flip=None, want_grads=True, want_zabs=False):
+            grad_norm_count=None, flip=None, want_grads=True, want_zabs=False, want_enc=True):
     """Forward + backward of one batch. Returns a dict with loss, grad_enc,
     grad_mlp, y, dx0, margin and optionally zabs (see the C header)."""
     th = _arr(theta, np.float64)
     mm = _arr(m, np.uint32).reshape(-1, 3)
     n = mm.shape[0]
     t = _arr(target, np.float64)
-    ge = np.zeros(cfg.n_enc, dtype=np.float64) if want_grads else None
+    ge = np.zeros(cfg.n_enc, dtype=np.float64) if (want_grads and want_enc) else None
     gm = np.zeros(cfg.n_mlp, dtype=np.float64) if want_grads else None
     y = np.zeros(n, dtype=np.float64)
     dx0 = np.zeros((n, cfg.in_dim), dtype=np.float64)

@@ -165,3 +165,37 @@ def extract_block(field, lo, hi, ghost: int = 1):
             t = t.index_select(ax, torch.as_tensor(r, device=field.device))
         return t.contiguous()
     return np.ascontiguousarray(field[np.ix_(idx[0], idx[1], idx[2])])
+
+
+def advected_torch(shape, seed: int, t: float, velocity=(3.0, 2.0, 1.0), nu: float | None = None,
+                   device="cuda", slope: float = -5.0 / 3.0):
+    """`advected` generated with torch.fft in float32 on ``device`` (for the
+    512^3 in situ series); returns a float32 tensor [z, y, x] in [0, 1]."""
+    import math
+
+    import torch
+
+    nz, ny, nx = shape
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    kz = torch.fft.fftfreq(nz, device=device) * nz
+    ky = torch.fft.fftfreq(ny, device=device) * ny
+    kx = torch.fft.rfftfreq(nx, device=device) * nx
+    KZ, KY, KX = kz.view(-1, 1, 1), ky.view(1, -1, 1), kx.view(1, 1, -1)
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    k = torch.sqrt(k2)
+    if nu is None:
+        kmax2 = (nx / 2) ** 2 + (ny / 2) ** 2 + (nz / 2) ** 2
+        nu = math.log(2.0) / (16.0 * kmax2)
+    amp = torch.where(k > 0, k.clamp_min(1e-30) ** ((slope - 2.0) / 2.0), torch.zeros_like(k))
+    amp = amp * torch.exp(-nu * k2 * t)
+    del k
+    phase = torch.rand(amp.shape, generator=g, dtype=torch.float32).to(device) * (2 * math.pi)
+    vx, vy, vz = velocity
+    phase = phase - 2 * math.pi * t * (KX * (vx / nx) + KY * (vy / ny) + KZ * (vz / nz))
+    coef = torch.polar(amp, phase)
+    del amp, phase, k2
+    f = torch.fft.irfftn(coef, s=shape, dim=(0, 1, 2))
+    del coef
+    f -= f.min()
+    f /= f.max()
+    return f.contiguous()
