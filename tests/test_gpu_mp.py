@@ -170,13 +170,18 @@ def test_fp16_training_equal_psnr(dv, orc, A):
     assert abs(p16 - p32) < 0.2, (p16, p32)
 
 
-def test_grouped_launch_models_are_independent(dv, A):
+@pytest.mark.parametrize("wave_models", [None, "1", "3"])
+def test_grouped_launch_models_are_independent(dv, A, monkeypatch, wave_models):
     # Four models in one grouped FP16 launch. Model 0 trained in the group
     # equals model 0 trained alone (same RNG slot) up to the reordering of
     # atomic sums, and perturbing model 2's volume leaves the other models
     # within that same reordering noise.
     from paper_2304_10516_gb300 import volumes
 
+    # wave_models: models trained per wave inside the launch (1: one model at
+    # a time; 3: waves of 3 + 1); None leaves the library's choice (one wave)
+    if wave_models:
+        monkeypatch.setenv("DVNR_WAVE_MODELS", wave_models)
     c = dict(P.configs_blobs64(), batch=2048)
     vols = [torch.from_numpy(volumes.blobs(32, seed=2000 + i)).cuda() for i in range(4)]
 
