@@ -214,7 +214,9 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
   const int64_t T = 1LL << enc->log2_T;
   lv.hash_mask = (uint32_t)(T - 1);
   lv.dense_mask = 0;
-  int64_t off = 0;
+  int64_t off = 0, ext = 0;
+  auto padded = [](int64_t v) { return (v + kParamAlign - 1) / kParamAlign * kParamAlign; };
+  m->lmap.L = lv.L;
   for (int l = 0; l < lv.L; ++l) {
     const double r = std::floor((double)enc->base_res * std::pow(enc->growth, (double)l));
     if (r > (double)(1 << 21)) {
@@ -227,9 +229,15 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
     const bool dense = verts <= T;
     if (dense) lv.dense_mask |= 1u << l;
     lv.off[l] = off;
-    off += (dense ? verts : T) * lv.F;
+    m->lmap.int_off[l] = off;
+    m->lmap.ext_off[l] = ext;
+    const int64_t len = (dense ? verts : T) * lv.F;
+    off = padded(off + len);
+    ext += len;
   }
-  m->n_enc = off;
+  m->n_enc = ext;
+  m->lmap.ext_off[lv.L] = ext;
+  m->lmap.int_off[lv.L] = off;
   int64_t w = off;
   const int W = mlp->width, H = mlp->n_hidden;
   for (int k = 0; k < H; ++k) {
@@ -241,13 +249,15 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
   m->w_off[H] = w;
   m->glorot[H] = std::sqrt(6.0 / (double)(W + 1));
   w += W;
-  m->n_params = w;
-  m->n_mlp = w - m->n_enc;
-  if (m->n_params >= (1LL << 31)) {
+  m->n_mlp = w - off;
+  m->n_params = m->n_enc + m->n_mlp;
+  m->lmap.ext_off[lv.L + 1] = m->n_params;
+  m->n_store = padded(w);
+  if (m->n_store >= (1LL << 31)) {
     delete m;
     return fail(DVNR_E_UNSUPPORTED, "more than 2^31 parameters");
   }
-  const size_t P = (size_t)m->n_params;
+  const size_t P = (size_t)m->n_store;
   const size_t b32 = align256(P * 4), b16 = align256(P * 2), bst = align256(sizeof(ModelState)),
                bq = align256((kQTab + 1) * sizeof(int32_t)), bap = align256(sizeof(AdamModelPtrs));
   ce = cudaMalloc(&m->block, 4 * b32 + b16 + bst + bq + bap);
@@ -273,8 +283,12 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
     delete m;
     return s;
   };
-  if ((rc = launch_init_params(m, seed, 0)) != DVNR_OK) return cleanup(rc);
   if ((ce = cudaMemset(m->m1, 0, 3 * b32)) != cudaSuccess) return cleanup(cuda_status(ce, "cudaMemset"));
+  // storage padding between level tables stays zero in theta and its FP16 copy
+  if ((ce = cudaMemset(m->theta, 0, b32)) != cudaSuccess ||
+      (ce = cudaMemset(m->theta16, 0, b16)) != cudaSuccess)
+    return cleanup(cuda_status(ce, "cudaMemset"));
+  if ((rc = launch_init_params(m, seed, 0)) != DVNR_OK) return cleanup(rc);
   if ((ce = cudaMemcpy(m->st, &st0, sizeof(st0), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(adam_ptrs_dev(m), &ap, sizeof(ap), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaDeviceSynchronize()) != cudaSuccess)
@@ -304,14 +318,30 @@ dvnr_status dvnr_param_count(dvnr_model m, int64_t* n_enc, int64_t* n_mlp) {
   return DVNR_OK;
 }
 
+namespace dvnr {
+namespace {
+// Copy between the compact host layout and storage, block by block.
+dvnr_status copy_blocks(dvnr_model m, float* host, const float* host_src, bool to_host) {
+  for (int b = 0; b <= m->lmap.L; ++b) {
+    const int64_t e0 = m->lmap.ext_off[b], len = m->lmap.ext_off[b + 1] - e0;
+    const int64_t i0 = m->lmap.int_off[b];
+    if (to_host)
+      DVNR_CUDA(cudaMemcpy(host + e0, m->theta + i0, (size_t)len * 4, cudaMemcpyDeviceToHost));
+    else
+      DVNR_CUDA(cudaMemcpy(m->theta + i0, host_src + e0, (size_t)len * 4, cudaMemcpyHostToDevice));
+  }
+  return DVNR_OK;
+}
+}  // namespace
+}  // namespace dvnr
+
 dvnr_status dvnr_get_weights(dvnr_model m, float* host, int64_t n) {
   if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
   if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
   DVNR_CUDA(cudaDeviceSynchronize());
-  DVNR_CUDA(cudaMemcpy(host, m->theta, (size_t)n * 4, cudaMemcpyDeviceToHost));
-  return DVNR_OK;
+  return copy_blocks(m, host, nullptr, true);
 }
 
 dvnr_status dvnr_set_weights(dvnr_model m, const float* host, int64_t n) {
@@ -320,12 +350,13 @@ dvnr_status dvnr_set_weights(dvnr_model m, const float* host, int64_t n) {
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
   DVNR_CUDA(cudaDeviceSynchronize());
-  DVNR_CUDA(cudaMemcpy(m->theta, host, (size_t)n * 4, cudaMemcpyHostToDevice));
+  if ((rc = copy_blocks(m, nullptr, host, false)) != DVNR_OK) return rc;
   if ((rc = launch_refresh_half(m, 0)) != DVNR_OK) return rc;
-  DVNR_CUDA(cudaMemset(m->m1, 0, (size_t)n * 4));
-  DVNR_CUDA(cudaMemset(m->m2, 0, (size_t)n * 4));
-  DVNR_CUDA(cudaMemset(m->grad, 0, (size_t)n * 4));
+  DVNR_CUDA(cudaMemset(m->m1, 0, (size_t)m->n_store * 4));
+  DVNR_CUDA(cudaMemset(m->m2, 0, (size_t)m->n_store * 4));
+  DVNR_CUDA(cudaMemset(m->grad, 0, (size_t)m->n_store * 4));
   if ((rc = launch_state_reset(m->st, 1.f, 0)) != DVNR_OK) return rc;
+  m->scale_initialized = false;
   DVNR_CUDA(cudaDeviceSynchronize());
   return DVNR_OK;
 }
@@ -338,7 +369,7 @@ dvnr_status dvnr_copy_weights(dvnr_model dst, dvnr_model src, void* stream) {
   dvnr_status rc = use_device(dst);
   if (rc != DVNR_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t n = (size_t)dst->n_params;
+  const size_t n = (size_t)dst->n_store;
   DVNR_CUDA(cudaMemcpyAsync(dst->theta, src->theta, n * 4, cudaMemcpyDeviceToDevice, s));
   DVNR_CUDA(cudaMemcpyAsync(dst->theta16, src->theta16, n * 2, cudaMemcpyDeviceToDevice, s));
   DVNR_CUDA(cudaMemcpyAsync(dst->st, src->st, 2 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
@@ -437,7 +468,7 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
       a.explicit_iter = false;
       for (int64_t step = 0; step < cfg->steps; ++step) {
         if ((rc = fp32_forward_backward(a, s)) != DVNR_OK) return rc;
-        if ((rc = launch_adam(adam_ptrs_dev(m), 1, m->n_params, h, s)) != DVNR_OK) return rc;
+        if ((rc = launch_adam(adam_ptrs_dev(m), 1, m->n_store, h, s)) != DVNR_OK) return rc;
       }
     }
   }

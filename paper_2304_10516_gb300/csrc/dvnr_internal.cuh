@@ -58,6 +58,22 @@ struct LevelTab {
   int64_t off[kMaxLevels];         // first parameter of level l
 };
 
+// Compact (ABI) parameter index -> index in the library's storage, where each
+// level's table and the MLP block start on a 32-parameter boundary (so that a
+// pair of adjacent FP16 entries is one aligned 8-byte load and a pair of FP32
+// gradient entries one aligned 16-byte reduction). Block L is the MLP.
+constexpr int64_t kParamAlign = 32;
+struct LayoutMap {
+  int32_t L;
+  int64_t ext_off[kMaxLevels + 2];  // block starts in the compact layout; [L+1] = end
+  int64_t int_off[kMaxLevels + 1];  // block starts in storage
+};
+__host__ __device__ inline int64_t ext_to_int(const LayoutMap& lm, int64_t i) {
+  int l = 0;
+  while (l < lm.L && i >= lm.ext_off[l + 1]) ++l;
+  return lm.int_off[l] + (i - lm.ext_off[l]);
+}
+
 // ------------------------------------------------------- device state ------
 // Per-model state that lives on the device so that whole training steps can
 // be captured in a CUDA graph and replayed.
@@ -118,7 +134,9 @@ struct dvnr_model_s {
   dvnr_mlp_cfg mlp{};
   dvnr::LevelTab lv{};
   int64_t dims[3] = {0, 0, 0};  // stored voxels per axis (ghost included)
-  int64_t n_enc = 0, n_mlp = 0, n_params = 0;
+  int64_t n_enc = 0, n_mlp = 0, n_params = 0;  // compact (ABI) counts
+  int64_t n_store = 0;          // parameters in storage (level tables padded)
+  dvnr::LayoutMap lmap{};       // compact index -> storage index
   int64_t w_off[dvnr::kMaxHidden + 1] = {};
   double glorot[dvnr::kMaxHidden + 1] = {};  // init limit of each matrix
   // parameter block: theta | m1 | m2 | grad (fp32), theta16, state, qtab

@@ -210,15 +210,46 @@ __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half*
         lattice(m.y, lv.N[l], by, fr[g][1]);
         lattice(m.z, lv.N[l], bz, fr[g][2]);
       }
+      if constexpr (F <= 2) {
+        // corners x and x+1 whose entries form an aligned pair {2j, 2j+1}
+        // (every even x on a hashed level, every even index on a dense one)
+        // come in one load of both entries
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (on) {
-          const uint32_t idx =
-              corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
-          HalfVec<F>::load(tab16 + lv.off[l] + (size_t)idx * F, v[g][k]);
-        } else {
+        for (int q = 0; q < 4; ++q) {
+          if (on) {
+            const uint32_t y = by + (q & 1), z = bz + (q >> 1);
+            const uint32_t i0 = corner_index(lv, l, bx, y, z);
+            const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
+            const __half* tab = tab16 + lv.off[l];
+            if (i1 == (i0 ^ 1u)) {
+              float both[2 * F];
+              HalfVec<2 * F>::load(tab + (size_t)(i0 & ~1u) * F, both);
+              const bool odd = (i0 & 1u) != 0u;  // corner x is the upper entry
 #pragma unroll
-          for (int f = 0; f < F; ++f) v[g][k][f] = 0.f;
+              for (int f = 0; f < F; ++f) {
+                v[g][2 * q][f] = odd ? both[F + f] : both[f];
+                v[g][2 * q + 1][f] = odd ? both[f] : both[F + f];
+              }
+            } else {
+              HalfVec<F>::load(tab + (size_t)i0 * F, v[g][2 * q]);
+              HalfVec<F>::load(tab + (size_t)i1 * F, v[g][2 * q + 1]);
+            }
+          } else {
+#pragma unroll
+            for (int f = 0; f < F; ++f) v[g][2 * q][f] = v[g][2 * q + 1][f] = 0.f;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if (on) {
+            const uint32_t idx =
+                corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+            HalfVec<F>::load(tab16 + lv.off[l] + (size_t)idx * F, v[g][k]);
+          } else {
+#pragma unroll
+            for (int f = 0; f < F; ++f) v[g][k][f] = 0.f;
+          }
         }
       }
     }
@@ -272,16 +303,48 @@ __device__ __forceinline__ bool scatter_from_tmem(const LevelTab& lv, float* __r
       float* tab = grad + lv.off[l];
 #pragma unroll
       for (int f = 0; f < F; ++f) bad |= !isfinite(d[q * F + f]);
+      if constexpr (F <= 2) {
+        // x-neighbour corners whose entries form an aligned pair {2j, 2j+1}
+        // go out as one vector reduction of both entries
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
-                        (((k >> 2) & 1) ? fz : 1.f - fz);
-        const uint32_t idx =
-            corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
-        float g[F];
+        for (int r = 0; r < 4; ++r) {
+          const uint32_t y = by + (r & 1), z = bz + (r >> 1);
+          const float wyz = ((r & 1) ? fy : 1.f - fy) * ((r >> 1) ? fz : 1.f - fz);
+          const float w0 = (1.f - fx) * wyz, w1 = fx * wyz;
+          const uint32_t i0 = corner_index(lv, l, bx, y, z);
+          const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
+          if (i1 == (i0 ^ 1u)) {
+            float g[2 * F];
+            const bool odd = (i0 & 1u) != 0u;
 #pragma unroll
-        for (int f = 0; f < F; ++f) g[f] = w * d[q * F + f];
-        red_add<F>(tab + (size_t)idx * F, g);
+            for (int f = 0; f < F; ++f) {
+              g[f] = (odd ? w1 : w0) * d[q * F + f];
+              g[F + f] = (odd ? w0 : w1) * d[q * F + f];
+            }
+            red_add<2 * F>(tab + (size_t)(i0 & ~1u) * F, g);
+          } else {
+            float g0[F], g1[F];
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+              g0[f] = w0 * d[q * F + f];
+              g1[f] = w1 * d[q * F + f];
+            }
+            red_add<F>(tab + (size_t)i0 * F, g0);
+            red_add<F>(tab + (size_t)i1 * F, g1);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
+                          (((k >> 2) & 1) ? fz : 1.f - fz);
+          const uint32_t idx =
+              corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+          float g[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f) g[f] = w * d[q * F + f];
+          red_add<F>(tab + (size_t)idx * F, g);
+        }
       }
     }
   }
@@ -1215,7 +1278,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   auto one_step = [&](cudaStream_t st) -> dvnr_status {
     dvnr_status rc = launch_train(p, W, F, n, st);
     if (rc != DVNR_OK) return rc;
-    return launch_adam(c->d_adam, n, m0->n_params, h, st);
+    return launch_adam(c->d_adam, n, m0->n_store, h, st);
   };
   int64_t left = cfg->steps;
   if (profiling_on() || left < 8) {

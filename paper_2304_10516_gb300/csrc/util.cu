@@ -25,10 +25,11 @@ struct InitArgs {
   float* theta;
   __half* theta16;
   int64_t n_params, n_enc;
-  int64_t bound[kMaxHidden + 1];  // end (exclusive) of matrix k
+  int64_t bound[kMaxHidden + 1];  // end (exclusive, compact index) of matrix k
   double limit[kMaxHidden + 1];
   int32_t n_mats;
   uint2 key;
+  LayoutMap lmap;
 };
 
 __global__ void k_init_params(InitArgs a) {
@@ -50,8 +51,9 @@ __global__ void k_init_params(InitArgs a) {
     const double span = __dsub_rn(hi, lo);
     const double v = __dadd_rn(lo, __dmul_rn(span, u));
     const float f = __double2float_rn(v);
-    a.theta[i] = f;
-    a.theta16[i] = __float2half_rn(f);
+    const int64_t j = ext_to_int(a.lmap, i);
+    a.theta[j] = f;
+    a.theta16[j] = __float2half_rn(f);
   }
 }
 
@@ -255,13 +257,17 @@ __global__ void k_state_reset(ModelState* st, float loss_scale) {
 
 // Hand out the gradient of one forward/backward without an optimiser step:
 // grad_out = grad / S, loss_out = loss_sum / B; then clear the accumulators.
-__global__ void k_finish_grad(float* __restrict__ grad, int64_t n, float inv_S,
-                              float* __restrict__ grad_out, ModelState* st, float inv_batch,
-                              float* __restrict__ loss_out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (grad_out) grad_out[i] = grad[i] * inv_S;
-    grad[i] = 0.f;
+__global__ void k_finish_grad(float* __restrict__ grad, int64_t n_params,
+                              LayoutMap lmap, float inv_S, float* __restrict__ grad_out,
+                              ModelState* st, float inv_batch, float* __restrict__ loss_out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // each storage entry belongs to one compact index, read and cleared by the
+  // same thread; the padding between level tables is never written
+  for (int64_t i = t0; i < n_params; i += stride) {
+    const int64_t j = ext_to_int(lmap, i);
+    if (grad_out) grad_out[i] = grad[j] * inv_S;
+    grad[j] = 0.f;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -305,8 +311,9 @@ dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_ba
                                float* loss_out, cudaStream_t s) {
   {
     ProfScope ps_("finish_grad", s);
-    k_finish_grad<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(
-      m->grad, m->n_params, 1.0f / loss_scale_used, grad_out, m->st, inv_batch, loss_out);
+    k_finish_grad<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(
+      m->grad, m->n_params, m->lmap, 1.0f / loss_scale_used, grad_out, m->st,
+      inv_batch, loss_out);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;
@@ -319,8 +326,11 @@ dvnr_status launch_init_params(dvnr_model m, uint64_t seed, cudaStream_t s) {
   a.n_params = m->n_params;
   a.n_enc = m->n_enc;
   a.n_mats = m->mlp.n_hidden + 1;
+  a.lmap = m->lmap;
+  // matrix bounds in compact indices: storage offset minus the MLP block shift
+  const int64_t shift = m->lmap.int_off[m->lmap.L] - m->lmap.ext_off[m->lmap.L];
   for (int k = 0; k <= m->mlp.n_hidden; ++k) {
-    a.bound[k] = (k < m->mlp.n_hidden) ? m->w_off[k + 1] : m->n_params;
+    a.bound[k] = (k < m->mlp.n_hidden) ? m->w_off[k + 1] - shift : m->n_params;
     a.limit[k] = m->glorot[k];
   }
   a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -335,8 +345,8 @@ dvnr_status launch_init_params(dvnr_model m, uint64_t seed, cudaStream_t s) {
 dvnr_status launch_refresh_half(dvnr_model m, cudaStream_t s) {
   {
     ProfScope ps_("refresh_half", s);
-    k_refresh_half<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(m->theta, m->theta16,
-                                                                     m->n_params);
+    k_refresh_half<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(m->theta, m->theta16,
+                                                                    m->n_store);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;
