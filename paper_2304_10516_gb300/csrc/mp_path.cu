@@ -715,12 +715,14 @@ teardown:
   if (warp == 0) umma::tmem_dealloc(tmem, p.lay.tmem_cols);
 }
 
-// Sum the per-CTA partial weight gradients (and losses) of every model: CTA
-// c covered tiles [T c / G, T (c+1) / G) of the model-major tile list, and
-// wrote model m into slot m - (its first model). A block sums 32 consecutive
-// entries (one per lane, coalesced) with its 8 warps splitting the CTAs, then
-// combines the warps in shared memory. The MLP gradients are zero before this
-// kernel (Adam clears them), so the sum is stored.
+// Sum the per-CTA partial weight gradients (and losses) of every model. In
+// wave w, CTA c covered the wave's tiles [Tw c / G, Tw (c+1) / G) and wrote
+// model m into slot w * slots_per_wave + (m - first model of its chunk);
+// CTAs whose chunk is empty or misses the model wrote nothing for it. A block
+// sums 32 consecutive entries (one per lane, coalesced) with its 8 warps
+// splitting the CTAs, then combines the warps in shared memory. The MLP
+// gradients are zero before this kernel (Adam clears them), so the sum is
+// stored.
 constexpr int kReduceWarps = 8;
 
 __global__ void __launch_bounds__(32 * kReduceWarps)
@@ -731,25 +733,38 @@ __global__ void __launch_bounds__(32 * kReduceWarps)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
   // the model's wave and its tiles relative to the wave (tile counts stay
-  // below 2^31 / G, so 32-bit products and quotients suffice)
+  // below 2^32 / G, so 32-bit products and quotients suffice)
   const int wv = m / models_per_wave, m_rel = m - wv * models_per_wave;
   const int64_t wb = (int64_t)wv * wave_tiles;
   const uint32_t Tw = (uint32_t)(wave_tiles < T - wb ? wave_tiles : T - wb);
   const uint32_t G32 = (uint32_t)G, tpm32 = (uint32_t)tpm;
   const uint32_t t0 = (uint32_t)m_rel * tpm32, t1 = t0 + tpm32;
-  uint32_t c0 = (uint32_t)(((uint64_t)t0 * G32) / Tw);
-  while (c0 > 0 && (Tw * c0) / G32 > t0) --c0;
-  while (c0 + 1 < G32 && (Tw * (c0 + 1)) / G32 <= t0) ++c0;
+  // CTAs whose chunk starts before t1 and ends after t0
+  uint32_t c_lo = (uint32_t)(((uint64_t)t0 * G32) / Tw);
+  while (c_lo > 0 && (Tw * c_lo) / G32 > t0) --c_lo;
+  while (c_lo < G32 && (Tw * (c_lo + 1)) / G32 <= t0) ++c_lo;
+  uint32_t c_hi = (uint32_t)(((uint64_t)t1 * G32 + Tw - 1) / Tw);
+  if (c_hi > G32) c_hi = G32;
+  while (c_hi < G32 && (Tw * c_hi) / G32 < t1) ++c_hi;
+  while (c_hi > c_lo && (Tw * (c_hi - 1)) / G32 >= t1) --c_hi;
   float sum = 0.f;
   if (j <= n_mlp) {
-    for (uint32_t c = c0 + warp; c < G32; c += kReduceWarps) {
-      const uint32_t begin = (Tw * c) / G32;
-      if (begin >= t1) break;
-      const uint32_t end = (Tw * (c + 1)) / G32;
-      if (end <= t0) continue;  // this CTA had no tile of the model
-      const uint32_t first = begin / tpm32;
-      const size_t slot = (size_t)wv * slots_per_wave + (size_t)(m_rel - first);
-      sum += __ldg(partial + ((size_t)c * slots + slot) * part_stride + j);
+    const float* base = partial + (size_t)wv * slots_per_wave * part_stride + j;
+    // batches of 8 CTAs per warp: all 8 (predicated) loads are issued before
+    // any is summed, so their latencies overlap
+    constexpr int kBatch = 8;
+    for (uint32_t cb = c_lo + warp; cb < c_hi; cb += kBatch * kReduceWarps) {
+      float v[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        const uint32_t c = cb + (uint32_t)(u * kReduceWarps);
+        const uint32_t b = (Tw * c) / G32, e = (Tw * (c + 1)) / G32;
+        const bool ok = c < c_hi && b < e;  // an empty chunk wrote nothing
+        const size_t off = ok ? ((size_t)c * slots + (m_rel - b / tpm32)) * part_stride : 0;
+        v[u] = ok ? __ldg(base + off) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) sum += v[u];
     }
   }
   __shared__ float s_part[kReduceWarps][32];
