@@ -241,7 +241,7 @@ def run_ours(args, rank, world, local_rank):
     ach = byt / (dms / dcnt / 1e3) / 1e9 if byt else None
     result["roofline"] = {
         "kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-        "frac": (ach / hbm_peak) if ach else None, "traffic": None,
+        "frac": (ach / hbm_peak) if ach else None, "traffic": measured_traffic(dom, args.workload),
         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
         "avg_launch_ms": dms / dcnt,
         "share": {k: round(v[0] / total, 4) for k, v in kern.items()},
@@ -343,6 +343,24 @@ def _roofline(kern, w, n_params, units, hbm_peak, have_peaks):
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if have_peaks else "fallback",
             "avg_launch_ms": dms / dcnt,
             "share": {k: round(v[0] / total, 4) for k, v in kern.items()}}
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch of the training kernel from the committed ncu
+    summary, if it was taken on the current kernel revision (else None)."""
+    import re
+
+    if kernel != "train_fused_fp16" or workload != "spectral256":
+        return None
+    try:
+        src = open(os.path.join(ROOT, "paper_2304_10516_gb300", "csrc", "mp_path.cu")).read()
+        rev = int(re.search(r"kTrainKernelRevision = (\d+);", src).group(1))
+        prof = open(os.path.join(ROOT, "profiles", "k_mp_train_fp16_spectral256.md")).read()
+        prev = int(re.search(r"kernel revision: (\d+)", prof).group(1))
+        traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", prof).group(1))
+    except Exception:
+        return None
+    return traffic if rev == prev else None
 
 
 def _peaks():

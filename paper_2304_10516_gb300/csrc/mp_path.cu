@@ -35,6 +35,18 @@ namespace dvnr {
 namespace {
 
 constexpr int kTile = 128;
+// Revision of the training kernel's memory behaviour; the DRAM-traffic figure
+// of an Nsight Compute capture is reported only while it matches.
+constexpr int kTrainKernelRevision = 7;
+#ifndef DVNR_DEC_PAIR
+#define DVNR_DEC_PAIR false
+#endif
+#ifndef DVNR_DEC_GROUP
+#define DVNR_DEC_GROUP 4
+#endif
+#ifndef DVNR_TRAIN_PAIR
+#define DVNR_TRAIN_PAIR true
+#endif
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s of SM clock per wait
 
 __device__ __forceinline__ uint32_t tile_off(uint32_t f, uint32_t s) {
@@ -189,18 +201,20 @@ __device__ __forceinline__ void st_row(uint8_t* base, uint32_t off, const float*
 
 // Hash-grid encoding of one coordinate, FP16 tables, FP32 interpolation,
 // written as FP16 to the sample's row of the ACT tile (feature 0 .. D-1).
-// The corner loads of kLevelGroup levels are issued together so that their
-// latencies overlap.
+// The corner loads of LG levels are issued together so that their latencies
+// overlap; with PAIR, x-neighbour corners in an aligned entry pair share one
+// load (training samples are scattered, so this saves requests; decoding walks
+// the grid in x order, where neighbouring lanes already share lines).
 constexpr int kLevelGroup = 4;
 
-template <int F>
+template <int F, bool PAIR = true, int LG = kLevelGroup>
 __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half* __restrict__ tab16,
                                                uint3 m, bool valid, uint8_t* act, uint32_t s) {
-  for (int l0 = 0; l0 < lv.L; l0 += kLevelGroup) {
-    float v[kLevelGroup][8][F];
-    float fr[kLevelGroup][3];
+  for (int l0 = 0; l0 < lv.L; l0 += LG) {
+    float v[LG][8][F];
+    float fr[LG][3];
 #pragma unroll
-    for (int g = 0; g < kLevelGroup; ++g) {
+    for (int g = 0; g < LG; ++g) {
       const int l = l0 + g;
       const bool on = valid && l < lv.L;
       uint32_t bx = 0, by = 0, bz = 0;
@@ -210,7 +224,7 @@ __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half*
         lattice(m.y, lv.N[l], by, fr[g][1]);
         lattice(m.z, lv.N[l], bz, fr[g][2]);
       }
-      if constexpr (F <= 2) {
+      if constexpr (PAIR && F <= 2) {
         // corners x and x+1 whose entries form an aligned pair {2j, 2j+1}
         // (every even x on a hashed level, every even index on a dense one)
         // come in one load of both entries
@@ -254,7 +268,7 @@ __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half*
       }
     }
 #pragma unroll
-    for (int g = 0; g < kLevelGroup; ++g) {
+    for (int g = 0; g < LG; ++g) {
       const int l = l0 + g;
       if (l >= lv.L) break;
       const float fx = fr[g][0], fy = fr[g][1], fz = fr[g][2];
@@ -504,7 +518,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     const uint3 mc = valid ? draw_sample(sp, (uint32_t)i, iter) : make_uint3(0u, 0u, 0u);
     VolCorners vc{};
     if (valid) vc = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc);  // in flight during the encode
-    encode_to_tile<F>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
+    encode_to_tile<F, DVNR_TRAIN_PAIR>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
     const float target = valid ? (vol_interp(vc) - vmin) * inv_range : 0.f;
     umma::fence_proxy_async();
     umma::fence_before_sync();
@@ -835,7 +849,7 @@ __global__ void __launch_bounds__(kTile) k_mp_decode(const __grid_constant__ MpD
                        dec_unit_to_fixed(p.xyz[3 * i + 2], p.origin[2], p.nstore[2]));
       }
     }
-    encode_to_tile<F>(p.lv, p.theta16, m, valid, s_act, (uint32_t)tid);
+    encode_to_tile<F, DVNR_DEC_PAIR, DVNR_DEC_GROUP>(p.lv, p.theta16, m, valid, s_act, (uint32_t)tid);
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
