@@ -37,6 +37,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2304_10516_gb300 import shard  # noqa: E402
+
 WORKLOADS = {
     "spectral256": dict(desc="256^3 spectral k^-5/3 field, L=16 F=2 T=2^19 N0=16 b=1.38, "
                              "MLP 32-64-64-64-1, batch 2^18",
@@ -185,14 +187,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     launches = lib.dvnr_launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = shard.max_over_ranks(e0.elapsed_time(e1))  # the slowest rank's time
     clk = clocks.stop()
     samples = w["batch"] * args.steps * world
     value = samples / (ms / 1e3)
@@ -399,6 +394,10 @@ def run_blocks(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(0 if "CUDA_VISIBLE_DEVICES" in os.environ else local_rank)
     dv.train(models, vols, cfg(max(args.warmup, 3)))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
     torch.cuda.synchronize()
     l0 = lib.dvnr_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -406,7 +405,7 @@ def run_blocks(args, rank, world, local_rank):
     dv.train(models, vols, cfg(args.steps), sync=False)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = shard.max_over_ranks(e0.elapsed_time(e1))
     launches = lib.dvnr_launch_count() - l0
     clk = clocks.stop()
     samples = n * w["batch"] * args.steps * world
@@ -534,6 +533,7 @@ def run_insitu(args, rank, world, local_rank):
         del field
     launches = lib.dvnr_launch_count() - l0
     clk = clocks.stop()
+    t_train = shard.max_over_ranks(t_train)
     T = w["t_steps"]
     samples = T * w["steps_full"] * w["batch"] * world
     res = {
