@@ -199,8 +199,12 @@ dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out);
  * volume first (min/max over all stored voxels).
  * FP16 precision: all n models run in one grouped kernel per step (they
  * must share one encoding and MLP configuration), the steps are replayed
- * from a CUDA graph. FP32 precision: the plain path, models one after
- * another.
+ * from a CUDA graph. The first FP16 call for a configuration (encoding, MLP,
+ * batch, number of models) times a few launch shapes of the training kernel
+ * on its models and volumes and keeps the fastest for the process; that call
+ * synchronises the stream once (parameters, moments and step counters are
+ * not changed by the trials; environment variable DVNR_AUTOTUNE=0 skips it).
+ * FP32 precision: the plain path, models one after another.
  * final_loss_host: if not NULL, receives n mean losses of the last step
  * and the call synchronises the stream.
  * Errors: DVNR_E_INVALID, DVNR_E_UNSUPPORTED, DVNR_E_CUDA,

@@ -24,7 +24,11 @@
 // collect unused products and are never read.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "mp_path.cuh"
@@ -37,7 +41,7 @@ namespace {
 constexpr int kTile = 128;
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
-constexpr int kTrainKernelRevision = 7;
+[[maybe_unused]] constexpr int kTrainKernelRevision = 7;
 #ifndef DVNR_DEC_PAIR
 #define DVNR_DEC_PAIR false
 #endif
@@ -1120,6 +1124,7 @@ struct MpCache {
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
   int models_per_wave = 0;
+  int ctas_per_sm = 0;
   void clear() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1177,7 +1182,7 @@ int train_grid(const MpParams& p) {
 // workload waves of 2 models train 1.34x faster than all 64 at once); the
 // DVNR_WAVE_MODELS environment variable overrides the choice. A CTA gets
 // one partial slot per model its contiguous run of a wave touches.
-void set_waves(MpParams& p, const dvnr_model m, int n_models) {
+int heuristic_models_per_wave(const MpParams& p, const dvnr_model m, int n_models) {
   int l2 = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
@@ -1186,12 +1191,11 @@ void set_waves(MpParams& p, const dvnr_model m, int n_models) {
   const int by_cache = (int)std::max(1.0, std::floor(0.25 * (double)l2 / per_model));
   const int64_t G0 = train_grid(p);
   const int by_occupancy = (int)((G0 + 2 * p.tiles_per_model - 1) / (2 * p.tiles_per_model));
-  int mw = std::max(by_cache, by_occupancy);
-  if (const char* e = getenv("DVNR_WAVE_MODELS")) {
-    const int v = atoi(e);
-    if (v > 0) mw = v;
-  }
-  mw = std::min(mw, n_models);
+  return std::min(std::max(by_cache, by_occupancy), n_models);
+}
+
+void set_waves(MpParams& p, int n_models, int mw) {
+  mw = std::max(1, std::min(mw, n_models));
   p.models_per_wave = mw;
   p.n_waves = (n_models + mw - 1) / mw;
   p.wave_tiles = (int64_t)mw * p.tiles_per_model;
@@ -1200,6 +1204,15 @@ void set_waves(MpParams& p, const dvnr_model m, int n_models) {
   const int64_t per = (tw + G - 1) / G;
   p.slots_per_wave = (int)((per + p.tiles_per_model - 1) / p.tiles_per_model + 1);
   p.slots_per_cta = p.n_waves * p.slots_per_wave;
+}
+
+void set_waves(MpParams& p, const dvnr_model m, int n_models) {
+  int mw = heuristic_models_per_wave(p, m, n_models);
+  if (const char* e = getenv("DVNR_WAVE_MODELS")) {
+    const int v = atoi(e);
+    if (v > 0) mw = v;
+  }
+  set_waves(p, n_models, mw);
 }
 
 size_t partial_floats(const MpParams& p) {
@@ -1220,6 +1233,104 @@ dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStre
                                      p.wave_tiles, p.models_per_wave, p.slots_per_wave);
   }
   DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+// Launch-shape autotuner of the grouped training kernel: on the first call
+// for a configuration (encoding, MLP, batch, number of models) it times the
+// fused kernel and its reduction for each candidate -- CTAs per SM (as many
+// as fit, or one) and models per wave (the heuristic, half, double) -- on the
+// call's own models and volumes, then clears what those trial runs wrote
+// (weight gradients, loss sums, overflow flags; parameters, moments and step
+// counters are not touched) and caches the fastest choice for the process.
+// DVNR_AUTOTUNE=0 keeps the heuristic; DVNR_WAVE_MODELS fixes the wave size.
+struct TuneChoice {
+  int ctas_per_sm;
+  int models_per_wave;
+};
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+
+std::string tune_key(const dvnr_model m, int n, const dvnr_train_cfg* cfg) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d:%.9g:%d:%d:%d:%d:%d", m->enc.n_levels, m->enc.n_features,
+           m->enc.log2_T, m->enc.base_res, m->mlp.width, m->enc.growth, m->mlp.n_hidden, cfg->batch, n,
+           cfg->lambda_bnd > 0.f ? 1 : 0, cfg->loss);
+  return buf;
+}
+
+dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, float** partial,
+                     size_t* partial_cap, TuneChoice* out, cudaStream_t s) {
+  std::vector<TuneChoice> cands;
+  const int h = heuristic_models_per_wave(base, models[0], n);
+  for (int ctas = base.lay.ctas_per_sm; ctas >= 1; ctas = ctas > 1 ? 1 : 0) {
+    MpParams q = base;
+    q.lay.ctas_per_sm = ctas;
+    const int hq = heuristic_models_per_wave(q, models[0], n);
+    for (int mw : {hq, std::max(1, hq / 2), std::min(n, 2 * hq)}) {
+      bool dup = false;
+      for (const auto& c : cands) dup |= c.ctas_per_sm == ctas && c.models_per_wave == mw;
+      if (!dup) cands.push_back({ctas, mw});
+    }
+    if (ctas == 1) break;
+  }
+  (void)h;
+  // scratch large enough for every candidate
+  size_t need = 0;
+  for (const auto& c : cands) {
+    MpParams q = base;
+    q.lay.ctas_per_sm = c.ctas_per_sm;
+    set_waves(q, n, c.models_per_wave);
+    need = std::max(need, partial_floats(q));
+  }
+  if (*partial_cap < need) {
+    if (*partial) {
+      DVNR_CUDA(cudaStreamSynchronize(s));
+      cudaFree(*partial);
+      *partial = nullptr;
+      *partial_cap = 0;
+    }
+    DVNR_CUDA(cudaMalloc(partial, need * sizeof(float)));
+    *partial_cap = need;
+  }
+  cudaEvent_t e0, e1;
+  DVNR_CUDA(cudaEventCreate(&e0));
+  DVNR_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  TuneChoice pick = cands[0];
+  dvnr_status rc = DVNR_OK;
+  for (const auto& c : cands) {
+    MpParams q = base;
+    q.lay.ctas_per_sm = c.ctas_per_sm;
+    set_waves(q, n, c.models_per_wave);
+    q.partial = *partial;
+    if ((rc = launch_train(q, W, F, n, s)) != DVNR_OK) break;  // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && rc == DVNR_OK; ++r) rc = launch_train(q, W, F, n, s);
+    cudaEventRecord(e1, s);
+    if (rc != DVNR_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = cuda_status(cudaGetLastError(), "autotune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // undo the trial runs' side effects
+  for (int i = 0; i < n; ++i) {
+    dvnr_model m = models[i];
+    DVNR_CUDA(cudaMemsetAsync(m->grad, 0, (size_t)m->n_store * sizeof(float), s));
+    DVNR_CUDA(cudaMemsetAsync(&m->st->loss_sum, 0, sizeof(float), s));
+    DVNR_CUDA(cudaMemsetAsync(&m->st->overflow, 0, sizeof(uint32_t), s));
+  }
+  if (rc != DVNR_OK) return rc;
+  *out = pick;
   return DVNR_OK;
 }
 
@@ -1281,8 +1392,37 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     return DVNR_E_UNSUPPORTED;
   }
   p.models = c->d_models;
-  set_waves(p, m0, n);
-  if (c->exec && c->models_per_wave != p.models_per_wave) {
+  {
+    const char* at = getenv("DVNR_AUTOTUNE");
+    const bool tune = !(at && atoi(at) == 0) && !getenv("DVNR_WAVE_MODELS") && !profiling_on();
+    const std::string key = tune_key(m0, n, cfg);
+    TuneChoice ch{0, 0};
+    bool have = false;
+    if (tune) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        ch = it->second;
+        have = true;
+      }
+    }
+    if (tune && !have) {
+      const int W0 = m0->mlp.width, F0 = m0->lv.F;
+      DVNR_WF_DISPATCH(W0, F0, set_smem_attr, true, lay.smem_bytes);
+      dvnr_status rc = autotune(p, models, n, W0, F0, &c->d_partial, &c->partial_cap, &ch, s);
+      if (rc != DVNR_OK) return rc;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = ch;
+      have = true;
+    }
+    if (have) {
+      p.lay.ctas_per_sm = ch.ctas_per_sm;
+      set_waves(p, n, ch.models_per_wave);
+    } else {
+      set_waves(p, m0, n);
+    }
+  }
+  if (c->exec && (c->models_per_wave != p.models_per_wave || c->ctas_per_sm != p.lay.ctas_per_sm)) {
     DVNR_CUDA(cudaStreamSynchronize(s));
     cudaGraphExecDestroy(c->exec);
     cudaGraphDestroy(c->graph);
@@ -1290,6 +1430,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     c->graph = nullptr;
   }
   c->models_per_wave = p.models_per_wave;
+  c->ctas_per_sm = p.lay.ctas_per_sm;
   const size_t need = partial_floats(p);
   if (c->partial_cap < need) {
     if (c->d_partial) {
