@@ -278,6 +278,8 @@ def run_ours(args, rank, world, local_rank):
     pinned = torch.from_numpy(vol_np).pin_memory()
     dvol = torch.empty_like(vol)
 
+    trained = {}
+
     def e2e(prec_code, reps):
         m = new_model(100 + rank)
         w0 = m.get_weights()
@@ -294,7 +296,10 @@ def run_ours(args, rank, world, local_rank):
         dec = m.decode_grid()
         sse, mx = dv.error_stats(dec, vol)
         mse = sse / vol.numel()
-        m.close()
+        if prec_code == precision:
+            trained["model"] = m
+        else:
+            m.close()
         return min(res), 10 * math.log10(1.0 / mse), mx, loss[0]
 
     clocks_e2e = ClockSampler(gpu_index)
@@ -309,6 +314,10 @@ def run_ours(args, rank, world, local_rank):
                       "max_abs": mx_mp, "fp32_max_abs": mx_32, "steps": steps_full}
     result["fp32_path"] = {"value": steps_full * w["batch"] / t_32, "unit": "train samples/s",
                            "speedup": t_32 / t_mp}
+
+    # ---- what the learned network gains: against the untrained network and
+    # against the raw-grid fallback (trilinear) at the model's FP16 byte size
+    result["learned_gain"] = learned_gain(trained.pop("model"), new_model(100 + rank), vol)
 
     # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
     result["cpu_baseline"] = cpu_baseline(w, vol_np)
@@ -553,6 +562,37 @@ def run_insitu(args, rank, world, local_rank):
         "per_step": per,
     }
     return res
+
+
+def learned_gain(model, untrained, vol):
+    """PSNR of the trained INR vs the untrained one and vs a grid of the same
+    FP16 byte budget (downsampled and read back by trilinear interpolation,
+    voxel centres aligned): the memory the representation saves and what that
+    memory buys when spent on a plain grid instead."""
+    import torch
+    import torch.nn.functional as Fn
+
+    from paper_2304_10516_gb300 import model as dv
+
+    def psnr_of(dec):
+        sse, mx = dv.error_stats(dec, vol)
+        return 10 * math.log10(1.0 / (sse / vol.numel())), mx
+
+    p_inr, mx_inr = psnr_of(model.decode_grid())
+    p_init, _ = psnr_of(untrained.decode_grid())
+    inr_bytes = model.n_params * 2
+    side = int(math.floor((inr_bytes / 2) ** (1.0 / 3.0)))
+    v5 = vol[None, None]
+    small = Fn.interpolate(v5, size=(side,) * 3, mode="trilinear", align_corners=True).half().float()
+    back = Fn.interpolate(small, size=tuple(vol.shape), mode="trilinear", align_corners=True)[0, 0]
+    p_grid, mx_grid = psnr_of(back.contiguous())
+    model.close()
+    untrained.close()
+    raw = vol.numel() * 4
+    return {"inr_bytes_fp16": inr_bytes, "raw_bytes_fp32": raw, "compression_ratio": raw / inr_bytes,
+            "psnr_inr": p_inr, "max_abs_inr": mx_inr, "psnr_untrained": p_init,
+            "psnr_grid_same_bytes": p_grid, "max_abs_grid_same_bytes": mx_grid,
+            "grid_side_same_bytes": side}
 
 
 def cpu_baseline(w, vol_np, budget_s=12.0):

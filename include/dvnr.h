@@ -176,6 +176,15 @@ dvnr_status dvnr_param_count(dvnr_model m, int64_t* n_enc, int64_t* n_mlp);
 dvnr_status dvnr_get_weights(dvnr_model m, float* host, int64_t n);
 dvnr_status dvnr_set_weights(dvnr_model m, const float* host, int64_t n);
 
+/* Model export as 16-bit floats (Sec. 3.4 stores the weights as 16-bit
+ * floats): the FP16 copy of the parameters (binary16 round-to-nearest-even of
+ * the FP32 master weights), n = n_enc + n_mlp values in the compact layout of
+ * dvnr_get_weights, as IEEE binary16 bit patterns. Import sets the FP32
+ * master weights to the widened FP16 values, refreshes the FP16 copy and
+ * resets the optimiser state. Both synchronise.                             */
+dvnr_status dvnr_export_fp16(dvnr_model m, uint16_t* host, int64_t n);
+dvnr_status dvnr_import_fp16(dvnr_model m, const uint16_t* host, int64_t n);
+
 /* Weight caching (Sec. 3.5): initialise `dst` from `src` (same encoding and
  * MLP configuration), copying parameters and value range and resetting
  * dst's Adam moments and step counts. Asynchronous on `stream`.            */

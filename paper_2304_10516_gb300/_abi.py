@@ -28,7 +28,7 @@ EXPORTS = [
     "dvnr_get_state", "dvnr_train", "dvnr_train_grad", "dvnr_decode_points", "dvnr_decode_grid",
     "dvnr_render", "dvnr_error_stats", "dvnr_corner_indices", "dvnr_profile_enable",
     "dvnr_profile_read", "dvnr_launch_count", "dvnr_selftest_umma",
-    "dvnr_error_stats_noalloc",
+    "dvnr_error_stats_noalloc", "dvnr_export_fp16", "dvnr_import_fp16",
 ]
 
 
@@ -102,6 +102,8 @@ _SIGS = {
     "dvnr_launch_count": ([], C.c_int64),
     "dvnr_selftest_umma": ([_P], C.c_int),
     "dvnr_error_stats_noalloc": ([_P, _P, C.c_int64, _P, _P], C.c_int),
+    "dvnr_export_fp16": ([_P, _P, C.c_int64], C.c_int),
+    "dvnr_import_fp16": ([_P, _P, C.c_int64], C.c_int),
 }
 
 

@@ -335,6 +335,43 @@ dvnr_status copy_blocks(dvnr_model m, float* host, const float* host_src, bool t
 }  // namespace
 }  // namespace dvnr
 
+dvnr_status dvnr_export_fp16(dvnr_model m, uint16_t* host, int64_t n) {
+  if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
+  if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  if ((rc = launch_refresh_half(m, 0)) != DVNR_OK) return rc;  // the copy follows the master weights
+  DVNR_CUDA(cudaDeviceSynchronize());
+  for (int b = 0; b <= m->lmap.L; ++b) {
+    const int64_t e0 = m->lmap.ext_off[b], len = m->lmap.ext_off[b + 1] - e0;
+    DVNR_CUDA(cudaMemcpy(host + e0, m->theta16 + m->lmap.int_off[b], (size_t)len * 2,
+                         cudaMemcpyDeviceToHost));
+  }
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_import_fp16(dvnr_model m, const uint16_t* host, int64_t n) {
+  if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
+  if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  for (int b = 0; b <= m->lmap.L; ++b) {
+    const int64_t e0 = m->lmap.ext_off[b], len = m->lmap.ext_off[b + 1] - e0;
+    DVNR_CUDA(cudaMemcpy(m->theta16 + m->lmap.int_off[b], host + e0, (size_t)len * 2,
+                         cudaMemcpyHostToDevice));
+  }
+  if ((rc = launch_widen_half(m, 0)) != DVNR_OK) return rc;
+  DVNR_CUDA(cudaMemset(m->m1, 0, (size_t)m->n_store * 4));
+  DVNR_CUDA(cudaMemset(m->m2, 0, (size_t)m->n_store * 4));
+  DVNR_CUDA(cudaMemset(m->grad, 0, (size_t)m->n_store * 4));
+  if ((rc = launch_state_reset(m->st, 1.f, 0)) != DVNR_OK) return rc;
+  m->scale_initialized = false;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  return DVNR_OK;
+}
+
 dvnr_status dvnr_get_weights(dvnr_model m, float* host, int64_t n) {
   if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
   if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);

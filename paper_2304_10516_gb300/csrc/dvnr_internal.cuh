@@ -279,6 +279,7 @@ __device__ __forceinline__ void value_range(const ModelState* st, float& vmin, f
 // Model-independent kernels (util.cu)
 dvnr_status launch_init_params(dvnr_model m, uint64_t seed, cudaStream_t s);
 dvnr_status launch_refresh_half(dvnr_model m, cudaStream_t s);
+dvnr_status launch_widen_half(dvnr_model m, cudaStream_t s);
 dvnr_status launch_minmax(const float* vol, int64_t n, ModelState* st, cudaStream_t s);
 dvnr_status launch_error_stats(const float* a, const float* b, int64_t n, double* out_dev,
                                cudaStream_t s);

@@ -64,6 +64,12 @@ __global__ void k_refresh_half(const float* __restrict__ theta, __half* __restri
     theta16[i] = __float2half_rn(theta[i]);
 }
 
+__global__ void k_widen_half(const __half* __restrict__ theta16, float* __restrict__ theta, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    theta[i] = __half2float(theta16[i]);
+}
+
 // Value range of a training volume (Sec. 3.1 normalises values by the
 // partition's min and max, ghost layer included) and a NaN/Inf check.
 __global__ void k_minmax(const float* __restrict__ v, int64_t n, ModelState* st) {
@@ -347,6 +353,15 @@ dvnr_status launch_refresh_half(dvnr_model m, cudaStream_t s) {
     ProfScope ps_("refresh_half", s);
     k_refresh_half<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(m->theta, m->theta16,
                                                                     m->n_store);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_widen_half(dvnr_model m, cudaStream_t s) {
+  {
+    ProfScope ps_("widen_half", s);
+    k_widen_half<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(m->theta16, m->theta, m->n_store);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;

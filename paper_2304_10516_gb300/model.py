@@ -119,6 +119,17 @@ class Model:
         assert w.size == self.n_params
         A.call("dvnr_set_weights", self._h, w.ctypes.data, self.n_params)
 
+    def export_fp16(self) -> np.ndarray:
+        """The model as 16-bit floats (compact layout), e.g. for storage."""
+        out = np.empty(self.n_params, dtype=np.uint16)
+        A.call("dvnr_export_fp16", self._h, out.ctypes.data, self.n_params)
+        return out.view(np.float16)
+
+    def import_fp16(self, w16):
+        w = np.ascontiguousarray(w16, dtype=np.float16).view(np.uint16)
+        assert w.size == self.n_params
+        A.call("dvnr_import_fp16", self._h, w.ctypes.data, self.n_params)
+
     def copy_weights_from(self, src: "Model", stream=None):
         A.call("dvnr_copy_weights", self._h, src._h, _stream(stream))
 

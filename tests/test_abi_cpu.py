@@ -18,7 +18,7 @@ HEADER = os.path.join(ROOT, "include", "dvnr.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(dvnr_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(dvnr_\w+)\s*\(", src)))
 
 
 def test_library_exports_every_declared_symbol():

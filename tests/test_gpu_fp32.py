@@ -249,3 +249,18 @@ def test_weights_roundtrip_and_warm_start(dv):
     w = np.linspace(-1, 1, a.n_params).astype(np.float32)
     a.set_weights(w)
     np.testing.assert_array_equal(a.get_weights(), w)
+
+
+def test_fp16_export_import_roundtrip(dv):
+    # Sec. 3.4 stores the model as 16-bit floats: export is the binary16
+    # rounding of the master weights; importing it gives a model that decodes
+    # like the FP16 copy it came from
+    c = P.configs_blobs64()
+    a = _model(dv, c, seed=3, hi=(16, 16, 16))
+    w = a.get_weights()
+    w16 = a.export_fp16()
+    np.testing.assert_array_equal(w16, w.astype(np.float16))
+    b = _model(dv, c, seed=4, hi=(16, 16, 16))
+    b.import_fp16(w16)
+    np.testing.assert_array_equal(b.get_weights(), w16.astype(np.float32))
+    assert a.n_params * 2 == w16.nbytes  # the stored model size in bytes
