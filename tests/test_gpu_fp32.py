@@ -137,24 +137,40 @@ def test_fp32_training_psnr_matches_oracle(dv, orc):
     assert psnr_gpu > P.psnr(sse0 / vol.size) + 10.0
 
 
-def test_fp32_training_chaotic_regime_within_oracle_envelope(dv, orc):
-    # At lr = 1e-2 (the workload's setting) training is chaotic: a 1e-7
-    # relative perturbation of the initial weights moves the oracle's PSNR
-    # after 200 steps by up to ~3 dB. The GPU result must fall inside the
-    # envelope of perturbed oracle runs widened by 1 dB.
+def test_fp32_training_chaotic_regime_matches_oracle_ensemble(dv, orc):
+    # At lr = 1e-2 (the workload's setting) training is chaotic: a 1e-6
+    # relative perturbation of the initial weights moves the 200-step PSNR by
+    # several dB, so single runs cannot be compared. Both sides instead train
+    # the same K perturbed initialisations (FP32 values, widened exactly for
+    # the oracle) and the mean PSNRs of the two ensembles must agree within
+    # three standard errors of their difference (a two-sample z-test, floored
+    # at 0.5 dB); every GPU run must also reach the oracle's range +- 2 dB.
     from paper_2304_10516_gb300 import volumes
 
+    K = 12
     c = P.configs_blobs64()
     oc = P.oracle_cfg(c)
     vol = volumes.blobs(64, seed=1001)
-    psnr_gpu, _, _ = _gpu_train_psnr(dv, c, vol, 4242, 1e-2, 200, 99)
+    vt = torch.from_numpy(vol).cuda()
     th0 = orc.init_params(oc, 4242)
     rng = np.random.default_rng(1)
-    env = [_oracle_train_psnr(orc, oc, vol, th0, 1e-2, 200, 99, c["batch"])[0]]
-    for _ in range(3):
-        th = th0 * (1 + 1e-7 * rng.standard_normal(th0.size))
-        env.append(_oracle_train_psnr(orc, oc, vol, th, 1e-2, 200, 99, c["batch"])[0])
-    assert min(env) - 1.0 <= psnr_gpu <= max(env) + 1.0, (psnr_gpu, env)
+    p_gpu, p_orc = [], []
+    for _ in range(K):
+        th = (th0 * (1 + 1e-6 * rng.standard_normal(th0.size))).astype(np.float32)
+        m = _model(dv, c, seed=0)
+        m.set_weights(th)
+        cfg = dv.TrainConfig(batch=c["batch"], steps=200, lr=1e-2, seed=99)
+        dv.train([m], [vt], cfg)
+        sse, _ = dv.error_stats(m.decode_grid(), vt)
+        p_gpu.append(P.psnr(sse / vol.size))
+        m.close()
+        p_orc.append(_oracle_train_psnr(orc, oc, vol, th.astype(np.float64), 1e-2, 200, 99,
+                                        c["batch"])[0])
+    p_gpu, p_orc = np.array(p_gpu), np.array(p_orc)
+    se = math.sqrt(p_gpu.var(ddof=1) / K + p_orc.var(ddof=1) / K)
+    tol = max(0.5, 3.0 * se)
+    assert abs(p_gpu.mean() - p_orc.mean()) <= tol, (p_gpu, p_orc, tol)
+    assert p_orc.min() - 2.0 <= p_gpu.min() and p_gpu.max() <= p_orc.max() + 2.0, (p_gpu, p_orc)
 
 
 def test_decode_grid_and_points_match_oracle(dv, orc):
