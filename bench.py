@@ -465,6 +465,11 @@ def run_blocks(args, rank, world, local_rank):
     res["e2e"] = {"value": n * w["batch"] * w["steps_full"] / t_full, "unit": "train samples/s",
                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 4 * n,
                   "step": f"{w['steps_full']} grouped iterations of all 64 models, read losses"}
+    # iteration budget proportional to each block's voxel count (Sec. 3.2,
+    # N_epoch = 16), then the same with the early stop at the median of the
+    # moving-average losses that run ended with: models leave the grouped
+    # launch at different steps
+    res["adaptive_budget"] = adaptive_budget(models, vols, boxes, enc, mlp, w, rank)
     # plain FP32 path on the same blocks (one model after another), throughput only
     f32 = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
     dv.train(f32, vols, cfg(3, A.DVNR_FP32))
@@ -562,6 +567,52 @@ def run_insitu(args, rank, world, local_rank):
         "per_step": per,
     }
     return res
+
+
+def adaptive_budget(models, vols, boxes, enc, mlp, w, rank):
+    """Grouped training with per-model budgets ceil(N_vox / B) * 16 and then
+    with early stop as well; throughput counts the iterations each model ran."""
+    import statistics
+
+    import torch
+
+    from paper_2304_10516_gb300 import _abi as A
+    from paper_2304_10516_gb300 import model as dv
+
+    for m in models:
+        m.close()
+    out = {}
+    stop = 0.0
+    for name in ("budget", "budget_and_stop"):
+        ms_ = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
+        cfg = dv.TrainConfig(batch=w["batch"], epochs=16, lr=w["lr"], lambda_bnd=w["lam"],
+                             sigma_bnd=0.005, precision=A.DVNR_FP16, seed=7 + rank,
+                             stop_loss=stop, stop_decay=0.9)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dv.train(ms_, vols, cfg, sync=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = [m.state() for m in ms_]
+        iters = [s_["iter"] for s_ in st]
+        sse, vox = 0.0, 0
+        for m, v in zip(ms_, vols):
+            ref = v[1:-1, 1:-1, 1:-1].contiguous()
+            s2, _ = dv.error_stats(m.decode_grid(), ref)
+            sse += s2
+            vox += ref.numel()
+        out[name] = {"value": sum(iters) * w["batch"] / (ms / 1e3), "unit": "train samples/s",
+                     "ms": ms, "iterations_min": min(iters), "iterations_max": max(iters),
+                     "iterations_sum": sum(iters), "stopped_models": sum(s_["stopped"] for s_ in st),
+                     "psnr": 10 * math.log10(1.0 / (sse / vox))}
+        if name == "budget":
+            stop = statistics.median(s_["loss_ema"] for s_ in st)
+            out["stop_loss"] = stop
+        for m in ms_:
+            m.close()
+    return out
 
 
 def learned_gain(model, untrained, vol):

@@ -102,16 +102,34 @@ typedef struct {
  *                  grouped launch per step
  *   loss           DVNR_LOSS_L1 (paper) or DVNR_LOSS_L2
  *   growth_interval  FP16 path: finite steps before the loss scale doubles
- *   steps          iterations to run in this call (>= 0)
+ *   steps          N_train: fixed iteration count of this call (>= 0),
+ *                  used when epochs == 0
  *   seed           sampling seed; model i of the call uses RNG key
  *                  (seed, i) -- the Philox counter also carries the model's
- *                  iteration count, so repeated calls draw fresh samples.   */
+ *                  iteration count, so repeated calls draw fresh samples.
+ *   epochs         N_epoch (>= 0): when > 0 the iteration count of model i
+ *                  is ceil(N_vox_i / batch) * epochs, N_vox_i = its owned
+ *                  voxels (Sec. 3.2: iterations proportional to the voxel
+ *                  count of the partition)
+ *   min_steps      N_train^min (>= 0): every model's count is at least this,
+ *                  so N_train^max = max(min_steps, count) (Sec. 3.2)
+ *   stop_loss      early stop (Sec. 3.2): a model stops once the moving
+ *                  average of its training loss falls below stop_loss
+ *                  (0 = off, else > 0)
+ *   stop_decay     the moving average: m_1 = L_1, m_t = d m_{t-1} +
+ *                  (1 - d) L_t over the finite steps of this call,
+ *                  d = stop_decay in [0, 1)
+ * Models of one call keep their own budgets: a model that reached its
+ * N_train^max or its stop threshold does no further work in the call (its
+ * tiles leave the grouped launch) while the others go on.                    */
 typedef struct {
   float lr, beta1, beta2, eps, weight_decay;
   float lambda_bnd, sigma_bnd;
   int32_t batch, precision, loss, growth_interval;
   int64_t steps;
   uint64_t seed;
+  int64_t epochs, min_steps;
+  float stop_loss, stop_decay;
 } dvnr_train_cfg;
 
 /* Snapshot of a model (read synchronously by dvnr_get_state).              */
@@ -125,6 +143,11 @@ typedef struct {
   int64_t n_enc, n_mlp;    /* parameter counts                                  */
   int32_t precision;       /* precision used by decode/render                   */
   int32_t nonfinite_input; /* 1 when the last training volume held NaN/Inf      */
+  double loss_ema;         /* moving average of the loss in the last call       */
+                           /*   (-1 before the first finite step)               */
+  int64_t budget_end;      /* iteration at which the last call's budget ends    */
+  int32_t stopped;         /* 1 when the last call stopped on stop_loss         */
+  int32_t pad;
 } dvnr_state_info;
 
 /* Transfer function for dvnr_render: rgb = c0 + (c1 - c0) v and

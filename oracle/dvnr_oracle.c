@@ -644,6 +644,64 @@ double orc_train(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Iteration budget and early stop (Sec. 3.2). The paper makes the number of
+ * iterations proportional to the partition's voxel count, N_train^max =
+ * max(N_train^min, ceil(N_vox / N_batch) N_epoch), and lets training end
+ * once a moving average of the loss is below a user threshold. Readings
+ * (the paper is silent): N_vox counts the owned voxels (no ghost layer); the
+ * moving average is exponential with factor d, started at the first finite
+ * loss of the call; steps whose gradient was non-finite (skipped by Adam)
+ * count against the budget but not in the average; the test follows every
+ * step's update, so a call that stops after step t has applied t steps.   */
+int64_t orc_max_iterations(int64_t n_vox, int64_t batch, int64_t steps,
+                           int64_t epochs, int64_t min_steps) {
+  int64_t n = steps;
+  if (epochs > 0) n = ((n_vox + batch - 1) / batch) * epochs;
+  return n > min_steps ? n : min_steps;
+}
+
+int64_t orc_stop_step(const double* losses, const int32_t* finite, int64_t n,
+                      double decay, double stop_loss, double* ema_out) {
+  double m = -1.0;
+  int have = 0;
+  int64_t t = 0;
+  while (t < n) {
+    const double L = losses[t];
+    const int ok = finite ? finite[t] != 0 : 1;
+    t += 1;
+    if (!ok) continue;
+    m = have ? decay * m + (1.0 - decay) * L : L;
+    have = 1;
+    if (stop_loss > 0.0 && m < stop_loss) break;
+  }
+  if (ema_out) *ema_out = m;
+  return t;
+}
+
+int64_t orc_train_budget(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
+                         double* theta, double* mom1, double* mom2, const float* vol,
+                         int64_t nx, int64_t ny, int64_t nz, double vmin, double vmax,
+                         int64_t budget, double stop_loss, double decay,
+                         double* loss_hist, double* ema_out, int32_t* stopped_out) {
+  double m = -1.0;
+  int have = 0, stopped = 0;
+  int64_t t = 0;
+  while (t < budget && !stopped) {
+    const int64_t skipped_before = st->skipped;
+    const double L = orc_train(c, tc, st, theta, mom1, mom2, vol, nx, ny, nz, vmin, vmax, 1, NULL);
+    if (loss_hist) loss_hist[t] = L;
+    t += 1;
+    if (st->skipped != skipped_before) continue;  /* non-finite step */
+    m = have ? decay * m + (1.0 - decay) * L : L;
+    have = 1;
+    if (stop_loss > 0.0 && m < stop_loss) stopped = 1;
+  }
+  if (ema_out) *ema_out = m;
+  if (stopped_out) *stopped_out = stopped;
+  return t;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Inference (Sec. 3: "the neural network can output v on-demand for any
  * arbitrary coordinates", decoded value y (max - min) + min, Sec. 4.1 keeps
  * the value range). No clamp of y (reading: the paper is silent).          */

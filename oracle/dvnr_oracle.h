@@ -113,6 +113,32 @@ double orc_train(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
                  int64_t nx, int64_t ny, int64_t nz, double vmin, double vmax,
                  int64_t steps, double* loss_hist);
 
+/* Iteration budget of one training call (Sec. 3.2): the fixed count `steps`,
+ * or ceil(n_vox / batch) * epochs when epochs > 0, raised to min_steps:
+ * N_train^max = max(N_train^min, ceil(N_vox / N_batch) N_epoch).            */
+int64_t orc_max_iterations(int64_t n_vox, int64_t batch, int64_t steps,
+                           int64_t epochs, int64_t min_steps);
+
+/* Early stop (Sec. 3.2) over a recorded loss sequence: the moving average
+ * m_1 = L_1, m_t = d m_{t-1} + (1 - d) L_t over the finite steps (finite[t]
+ * != 0; a step whose gradient was non-finite leaves m unchanged), stopping
+ * after the first step with m_t < stop_loss (stop_loss 0: never). Returns
+ * the number of steps run (n if it never stops); *ema_out = m after them
+ * (-1 if no finite step).                                                   */
+int64_t orc_stop_step(const double* losses, const int32_t* finite, int64_t n,
+                      double decay, double stop_loss, double* ema_out);
+
+/* orc_train under the budget and early stop of one call: at most `budget`
+ * iterations, ending after the first whose moving average falls below
+ * stop_loss. Returns the iterations run; loss_hist (budget entries, may be
+ * NULL) receives their losses, *ema_out the final moving average and
+ * *stopped_out 1 if the threshold ended the call.                            */
+int64_t orc_train_budget(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
+                         double* theta, double* mom1, double* mom2, const float* vol,
+                         int64_t nx, int64_t ny, int64_t nz, double vmin, double vmax,
+                         int64_t budget, double stop_loss, double decay,
+                         double* loss_hist, double* ema_out, int32_t* stopped_out);
+
 void orc_decode_unit(const orc_cfg* c, const double* theta, int64_t n,
                      const uint32_t* m, int mixed, double vmin, double vmax,
                      double* out);

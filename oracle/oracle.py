@@ -108,6 +108,15 @@ def _lib_handle():
                                       _P, _P, _P, _P, C.c_int64, C.c_int64, C.c_int64,
                                       C.c_double, C.c_double, C.c_int64, _P]
             lib.orc_train.restype = C.c_double
+            lib.orc_max_iterations.argtypes = [C.c_int64] * 5
+            lib.orc_max_iterations.restype = C.c_int64
+            lib.orc_stop_step.argtypes = [_P, _P, C.c_int64, C.c_double, C.c_double, _P]
+            lib.orc_stop_step.restype = C.c_int64
+            lib.orc_train_budget.argtypes = [C.POINTER(_Cfg), C.POINTER(_TrainCfg),
+                                             C.POINTER(_State), _P, _P, _P, _P, C.c_int64,
+                                             C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                             C.c_int64, C.c_double, C.c_double, _P, _P, _P]
+            lib.orc_train_budget.restype = C.c_int64
             lib.orc_decode_unit.argtypes = [C.POINTER(_Cfg), _P, C.c_int64, _P, C.c_int,
                                             C.c_double, C.c_double, _P]
             lib.orc_grid_coord.argtypes = [C.c_int64, C.c_int64]
@@ -287,6 +296,41 @@ def train(cfg: Config, tc: TrainConfig, st: State, theta, mom1, mom2, vol, vmin,
     _lib_handle().orc_train(cfg.ref, tc.ref, st.ref, _ptr(theta), _ptr(mom1), _ptr(mom2), _ptr(v),
                             nx, ny, nz, float(vmin), float(vmax), steps, _ptr(hist))
     return hist
+
+
+def max_iterations(n_vox, batch, steps=0, epochs=0, min_steps=0):
+    """N_train^max of one call (Sec. 3.2)."""
+    return int(_lib_handle().orc_max_iterations(int(n_vox), int(batch), int(steps), int(epochs),
+                                                int(min_steps)))
+
+
+def stop_step(losses, decay, stop_loss, finite=None):
+    """(steps run, final moving average) of the Sec. 3.2 early stop applied
+    to a recorded loss sequence."""
+    L = _arr(losses, np.float64)
+    fin = None if finite is None else _arr(finite, np.int32)
+    ema = C.c_double()
+    n = _lib_handle().orc_stop_step(_ptr(L), None if fin is None else _ptr(fin), L.size,
+                                    float(decay), float(stop_loss), C.byref(ema))
+    return int(n), ema.value
+
+
+def train_budget(cfg: Config, tc: TrainConfig, st: State, theta, mom1, mom2, vol, vmin, vmax,
+                 budget, stop_loss=0.0, decay=0.9):
+    """Training under the budget and early stop of one call (Sec. 3.2), in
+    place; returns (steps run, loss history, final moving average, stopped)."""
+    v = _arr(vol, np.float32)
+    nz, ny, nx = v.shape
+    hist = np.zeros(max(int(budget), 1), dtype=np.float64)
+    for a in (theta, mom1, mom2):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    ema = C.c_double()
+    stopped = C.c_int32()
+    n = _lib_handle().orc_train_budget(cfg.ref, tc.ref, st.ref, _ptr(theta), _ptr(mom1),
+                                       _ptr(mom2), _ptr(v), nx, ny, nz, float(vmin), float(vmax),
+                                       int(budget), float(stop_loss), float(decay), _ptr(hist),
+                                       C.byref(ema), C.byref(stopped))
+    return int(n), hist[:n], ema.value, bool(stopped.value)
 
 
 def decode_unit(cfg: Config, theta, m, vmin, vmax, mixed=False):

@@ -55,14 +55,18 @@ class dvnr_train_cfg(C.Structure):
     _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
                 ("weight_decay", C.c_float), ("lambda_bnd", C.c_float), ("sigma_bnd", C.c_float),
                 ("batch", C.c_int32), ("precision", C.c_int32), ("loss", C.c_int32),
-                ("growth_interval", C.c_int32), ("steps", C.c_int64), ("seed", C.c_uint64)]
+                ("growth_interval", C.c_int32), ("steps", C.c_int64), ("seed", C.c_uint64),
+                ("epochs", C.c_int64), ("min_steps", C.c_int64), ("stop_loss", C.c_float),
+                ("stop_decay", C.c_float)]
 
 
 class dvnr_state_info(C.Structure):
     _fields_ = [("vmin", C.c_double), ("vmax", C.c_double), ("loss_scale", C.c_double),
                 ("last_loss", C.c_double), ("iter", C.c_int64), ("adam_t", C.c_int64),
                 ("skipped", C.c_int64), ("n_enc", C.c_int64), ("n_mlp", C.c_int64),
-                ("precision", C.c_int32), ("nonfinite_input", C.c_int32)]
+                ("precision", C.c_int32), ("nonfinite_input", C.c_int32),
+                ("loss_ema", C.c_double), ("budget_end", C.c_int64), ("stopped", C.c_int32),
+                ("pad", C.c_int32)]
 
 
 class dvnr_tf(C.Structure):

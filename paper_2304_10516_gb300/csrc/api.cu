@@ -112,7 +112,26 @@ dvnr_status check_train_cfg(const dvnr_train_cfg* c) {
     return fail(DVNR_E_INVALID, "loss must be DVNR_LOSS_L1 or DVNR_LOSS_L2");
   if (c->precision == DVNR_FP16 && c->growth_interval < 1)
     return fail(DVNR_E_INVALID, "growth_interval must be >= 1");
+  if (c->epochs < 0 || c->min_steps < 0) return fail(DVNR_E_INVALID, "epochs and min_steps must be >= 0");
+  if (!(c->stop_loss >= 0.f) || !std::isfinite(c->stop_loss))
+    return fail(DVNR_E_INVALID, "stop_loss must be finite and >= 0");
+  if (!(c->stop_decay >= 0.f && c->stop_decay < 1.f)) return fail(DVNR_E_INVALID, "stop_decay must be in [0, 1)");
   return DVNR_OK;
+}
+
+// Iterations of one training call for model m (Sec. 3.2):
+// N_train^max = max(N_train^min, N_train), where N_train is the fixed count
+// `steps`, or ceil(N_vox / N_batch) * N_epoch (N_vox the owned voxels of the
+// partition) when epochs > 0.
+int64_t train_budget(const dvnr_model m, const dvnr_train_cfg* c) {
+  int64_t n = c->steps;
+  if (c->epochs > 0) {
+    const int64_t nvox = (m->box.hi[0] - m->box.lo[0]) * (m->box.hi[1] - m->box.lo[1]) *
+                         (m->box.hi[2] - m->box.lo[2]);
+    const int64_t per_epoch = (nvox + c->batch - 1) / c->batch;
+    n = per_epoch > INT64_MAX / c->epochs ? INT64_MAX : per_epoch * c->epochs;
+  }
+  return std::max(c->min_steps, n);
 }
 
 dvnr_status use_device(dvnr_model m) {
@@ -159,6 +178,9 @@ AdamHyper adam_hyper(const dvnr_train_cfg* cfg, bool mixed) {
   h.inv_batch = 1.0f / (float)cfg->batch;
   h.mixed = mixed ? 1 : 0;
   h.growth_interval = cfg->growth_interval > 0 ? cfg->growth_interval : (1 << 30);
+  h.gated = 1;
+  h.stop_loss = cfg->stop_loss;
+  h.stop_decay = cfg->stop_decay;
   return h;
 }
 
@@ -450,6 +472,10 @@ dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out) {
   out->n_mlp = m->n_mlp;
   out->precision = m->precision;
   out->nonfinite_input = st.nonfinite ? 1 : 0;
+  out->loss_ema = st.loss_ema;
+  out->budget_end = st.stop_at;
+  out->stopped = st.stopped ? 1 : 0;
+  out->pad = 0;
   if (st.timeouts) return fail(DVNR_E_TIMEOUT, "a bounded device wait gave up (%u)", st.timeouts);
   if (st.nonfinite) return fail(DVNR_E_NONFINITE_INPUT, "the last training volume held NaN/Inf");
   return DVNR_OK;
@@ -476,10 +502,18 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
         return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
     }
   }
+  std::vector<int64_t> budget((size_t)n);
+  int64_t max_budget = 0;
+  for (int i = 0; i < n; ++i) {
+    budget[i] = train_budget(models[i], cfg);
+    if (budget[i] > 0x7FFFFFFF) return fail(DVNR_E_INVALID, "model %d: iteration budget above 2^31 - 1", i);
+    max_budget = std::max(max_budget, budget[i]);
+  }
   if ((rc = use_device(models[0])) != DVNR_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < n; ++i) {
     dvnr_model m = models[i];
+    if ((rc = launch_begin_call(m->st, (uint32_t)budget[i], s)) != DVNR_OK) return rc;
     if (cfg->lambda_bnd > 0.f && (rc = prepare_qtab(m, cfg->sigma_bnd, s)) != DVNR_OK) return rc;
     if ((rc = launch_minmax(vol_dev[i], stored_voxels(m), m->st, s)) != DVNR_OK) return rc;
     m->precision = cfg->precision;
@@ -490,8 +524,9 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
   }
   const AdamHyper h = adam_hyper(cfg, mixed);
   if (mixed) {
-    rc = mp_train(models, n, vol_dev, cfg, h, s);
-    if (rc != DVNR_OK) return rc;
+    const bool uniform = std::all_of(budget.begin(), budget.end(), [&](int64_t b) { return b == max_budget; });
+    if (max_budget > 0 && (rc = mp_train(models, n, vol_dev, cfg, h, max_budget, uniform, s)) != DVNR_OK)
+      return rc;
   } else {
     for (int i = 0; i < n; ++i) {
       dvnr_model m = models[i];
@@ -503,7 +538,9 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
       a.batch = cfg->batch;
       a.loss = cfg->loss;
       a.explicit_iter = false;
-      for (int64_t step = 0; step < cfg->steps; ++step) {
+      a.gated = true;
+      // the kernels of a step do nothing once the model stopped early
+      for (int64_t step = 0; step < budget[i]; ++step) {
         if ((rc = fp32_forward_backward(a, s)) != DVNR_OK) return rc;
         if ((rc = launch_adam(adam_ptrs_dev(m), 1, m->n_store, h, s)) != DVNR_OK) return rc;
       }

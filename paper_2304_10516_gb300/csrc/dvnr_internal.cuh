@@ -90,8 +90,19 @@ struct ModelState {
   float loss_sum;             // sum of per-sample losses of this step
   float last_loss;            // mean loss of the last completed step
   uint32_t timeouts;          // bounded device waits that gave up
-  uint32_t pad[3];
+  // iteration budget and early stop of the current training call (Sec. 3.2)
+  uint32_t stop_at;           // the call ends this model's training at iter == stop_at
+  float loss_ema;             // moving average of the loss in this call (< 0: none yet)
+  uint32_t stopped;           // the moving average fell below the stop threshold
 };
+
+// A model takes part in a training step while its call's budget lasts and it
+// has not met the stop threshold. Every kernel of a step evaluates this on
+// the same state: only the last block of Adam changes it, after all the
+// step's other reads.
+__host__ __device__ inline bool model_active(const ModelState* st) {
+  return st->iter < st->stop_at && st->stopped == 0u;
+}
 
 __host__ __device__ inline uint32_t float_to_ordered(float f) {
 #ifdef __CUDA_ARCH__
@@ -280,6 +291,7 @@ __device__ __forceinline__ void value_range(const ModelState* st, float& vmin, f
 dvnr_status launch_init_params(dvnr_model m, uint64_t seed, cudaStream_t s);
 dvnr_status launch_refresh_half(dvnr_model m, cudaStream_t s);
 dvnr_status launch_widen_half(dvnr_model m, cudaStream_t s);
+dvnr_status launch_begin_call(ModelState* st, uint32_t budget, cudaStream_t s);
 dvnr_status launch_minmax(const float* vol, int64_t n, ModelState* st, cudaStream_t s);
 dvnr_status launch_error_stats(const float* a, const float* b, int64_t n, double* out_dev,
                                cudaStream_t s);
@@ -298,6 +310,8 @@ struct AdamHyper {
   float lr, beta1, beta2, eps, weight_decay;
   float inv_batch;
   int32_t mixed, growth_interval;
+  int32_t gated;               // skip models that are not model_active
+  float stop_loss, stop_decay; // early stop (stop_loss 0: off)
 };
 dvnr_status launch_adam(const AdamModelPtrs* models_dev, int n_models, int64_t n_params,
                         const AdamHyper& h, cudaStream_t s);
@@ -311,6 +325,7 @@ struct Fp32StepArgs {
   int32_t loss;
   bool explicit_iter;
   uint32_t iter;
+  bool gated;  // every kernel of the step returns at once when !model_active
   // optional debug outputs
   float* y_out;
   float* dx0_out;

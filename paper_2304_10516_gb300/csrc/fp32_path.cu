@@ -79,7 +79,9 @@ __global__ void k_sample_encode(LevelTab lv, const float* __restrict__ theta,
                                 const float* __restrict__ vol, int nx, int ny, int nz,
                                 SampleParams sp, const ModelState* __restrict__ st, int32_t batch,
                                 int use_iter, uint32_t iter_arg, float* __restrict__ x0,
-                                float* __restrict__ tgt, uint32_t* __restrict__ coords) {
+                                float* __restrict__ tgt, uint32_t* __restrict__ coords,
+                                int gated) {
+  if (gated && !model_active(st)) return;  // the model's call is over (budget or early stop)
   const uint32_t iter = use_iter ? iter_arg : st->iter;
   float vmin, inv_range;
   value_range(st, vmin, inv_range);
@@ -106,7 +108,8 @@ template <bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(256)
     k_sgemm64(const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
               float* __restrict__ C, int ldc, const float* __restrict__ aux, int M, int N, int K,
-              int kchunk) {
+              int kchunk, const ModelState* __restrict__ gate) {
+  if (gate && !model_active(gate)) return;
   __shared__ float As[16][64 + 4];
   __shared__ float Bs[16][64 + 4];
   const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
@@ -170,13 +173,14 @@ __global__ void __launch_bounds__(256)
 
 template <bool TA, bool TB, int EPI>
 dvnr_status gemm(const float* A, int lda, const float* B, int ldb, float* C, int ldc,
-                 const float* aux, int M, int N, int K, int splits, cudaStream_t s) {
+                 const float* aux, int M, int N, int K, int splits, cudaStream_t s,
+                 const ModelState* gate = nullptr) {
   const int kchunk = ((K + splits - 1) / splits + 15) / 16 * 16;
   splits = (K + kchunk - 1) / kchunk;
   dim3 grid((M + 63) / 64, (N + 63) / 64, std::max(splits, 1));
   {
     ProfScope ps_("fp32_gemm", s);
-    k_sgemm64<TA, TB, EPI><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, aux, M, N, K, kchunk);
+    k_sgemm64<TA, TB, EPI><<<grid, 256, 0, s>>>(A, lda, B, ldb, C, ldc, aux, M, N, K, kchunk, gate);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;
@@ -190,7 +194,8 @@ __global__ void __launch_bounds__(128)
     k_out_loss(const float* __restrict__ hH, const float* __restrict__ wout, int W,
                const float* __restrict__ tgt, int32_t batch, int32_t loss, float inv_B,
                float* __restrict__ dzH, float* __restrict__ gwout, ModelState* st,
-               float* __restrict__ y_out) {
+               float* __restrict__ y_out, int gated) {
+  if (gated && !model_active(st)) return;
   __shared__ float s_g[256];
   __shared__ float s_w[256];
   for (int j = threadIdx.x; j < W; j += blockDim.x) {
@@ -235,7 +240,8 @@ __global__ void __launch_bounds__(128)
 template <int F>
 __global__ void k_scatter(LevelTab lv, const uint32_t* __restrict__ coords,
                           const float* __restrict__ dx0, int32_t batch, float* __restrict__ grad,
-                          ModelState* st, float* __restrict__ dx0_out) {
+                          ModelState* st, float* __restrict__ dx0_out, int gated) {
+  if (gated && !model_active(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch; i += gridDim.x * blockDim.x) {
     const uint3 m = make_uint3(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2]);
     const float* d = dx0 + (size_t)i * lv.in_dim;
@@ -372,6 +378,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   const int nx = (int)m->dims[0], ny = (int)m->dims[1], nz = (int)m->dims[2];
   const int enc_blocks = std::min((B + 127) / 128, 152 * 16);
   uint32_t* coords = a.coords_out ? a.coords_out : ws.coords;
+  const ModelState* gate = a.gated ? m->st : nullptr;
   {
   ProfScope ps_("fp32_sample_encode", s);
   switch (m->lv.F) {
@@ -379,7 +386,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   case F:                                                                                        \
     k_sample_encode<F><<<enc_blocks, 128, 0, s>>>(m->lv, m->theta, a.vol, nx, ny, nz, a.sp,     \
                                                   m->st, B, a.explicit_iter ? 1 : 0, a.iter,    \
-                                                  ws.x0, ws.tgt, coords);                       \
+                                                  ws.x0, ws.tgt, coords, a.gated ? 1 : 0);      \
     break;
     DVNR_SE(1) DVNR_SE(2) DVNR_SE(4) DVNR_SE(8)
 #undef DVNR_SE
@@ -395,7 +402,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   for (int k = 0; k < H; ++k) {
     float* outp = ws.act + (size_t)k * B * W;
     rc = gemm<false, true, EPI_RELU>(in, in_dim, m->theta + m->w_off[k], in_dim, outp, W, nullptr,
-                                     B, W, in_dim, 1, s);
+                                     B, W, in_dim, 1, s, gate);
     if (rc != DVNR_OK) return rc;
     in = outp;
     in_dim = W;
@@ -408,7 +415,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   ProfScope ps_("fp32_out_loss", s);
   k_out_loss<<<(B + 127) / 128, 128, 0, s>>>(hH, m->theta + m->w_off[H], W, ws.tgt, B, a.loss,
                                              1.0f / (float)B, dz, m->grad + m->w_off[H], m->st,
-                                             a.y_out);
+                                             a.y_out, a.gated ? 1 : 0);
   }
   DVNR_CUDA(cudaGetLastError());
   const int splits = std::max(1, std::min(1024, B / 1024));
@@ -418,14 +425,14 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
     const int nin = (k == 1) ? D : W;
     float* gW = m->grad + m->w_off[k - 1];
     const float* Wk = m->theta + m->w_off[k - 1];
-    rc = gemm<true, false, EPI_ATOMIC>(dz, W, hprev, nin, gW, nin, nullptr, W, nin, B, splits, s);
+    rc = gemm<true, false, EPI_ATOMIC>(dz, W, hprev, nin, gW, nin, nullptr, W, nin, B, splits, s, gate);
     if (rc != DVNR_OK) return rc;
     if (k > 1) {
-      rc = gemm<false, false, EPI_MASK>(dz, W, Wk, nin, dz_other, nin, hprev, B, nin, W, 1, s);
+      rc = gemm<false, false, EPI_MASK>(dz, W, Wk, nin, dz_other, nin, hprev, B, nin, W, 1, s, gate);
       if (rc != DVNR_OK) return rc;
       std::swap(dz, dz_other);
     } else {
-      rc = gemm<false, false, EPI_STORE>(dz, W, Wk, nin, ws.dx0, nin, nullptr, B, nin, W, 1, s);
+      rc = gemm<false, false, EPI_STORE>(dz, W, Wk, nin, ws.dx0, nin, nullptr, B, nin, W, 1, s, gate);
       if (rc != DVNR_OK) return rc;
     }
   }
@@ -435,7 +442,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
 #define DVNR_SC(F)                                                                               \
   case F:                                                                                        \
     k_scatter<F><<<enc_blocks, 128, 0, s>>>(m->lv, coords, ws.dx0, B, m->grad, m->st,          \
-                                            a.dx0_out);                                          \
+                                            a.dx0_out, a.gated ? 1 : 0);                         \
     break;
     DVNR_SC(1) DVNR_SC(2) DVNR_SC(4) DVNR_SC(8)
 #undef DVNR_SC

@@ -105,6 +105,11 @@ struct MpParams {
   // gradients in use at any time stay within L2
   int64_t wave_tiles;
   int32_t n_waves, models_per_wave, slots_per_wave;
+  // models of the step: sched[0] = n_active, sched[1 + a] = index of the
+  // a-th active model, sched[1 + n_models + m] = position of model m (-1 when
+  // inactive), written by k_mp_schedule; nullptr = all n_models take part
+  const int32_t* sched;
+  int32_t n_models;
 };
 
 struct MpDecodeParams {
@@ -413,6 +418,12 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
   const float* s_wout = reinterpret_cast<const float*>(smem + p.lay.smem_wout);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int D = p.D, H = p.H;
+  // the step's active models (uniform over the grid; nothing to do when every
+  // model has spent its budget or stopped)
+  const int n_act = p.sched ? p.sched[0] : p.n_models;
+  if (n_act <= 0) return;
+  const int64_t T_act = (int64_t)n_act * p.tiles_per_model;
+  const int n_waves = (n_act + p.models_per_wave - 1) / p.models_per_wave;
 
   if (tid == 0) {
     umma::mbar_init(mbar, 1);
@@ -492,19 +503,22 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     __syncthreads();
   };
 
-  for (int wv = 0; wv < p.n_waves; ++wv) {
+  // tiles are numbered over the active models in order (position a covers
+  // tiles [a tpm, (a + 1) tpm)); the waves split that sequence
+  for (int wv = 0; wv < n_waves; ++wv) {
   const int64_t wb = (int64_t)wv * p.wave_tiles;
-  const int64_t Tw = p.wave_tiles < p.total_tiles - wb ? p.wave_tiles : p.total_tiles - wb;
+  const int64_t Tw = p.wave_tiles < T_act - wb ? p.wave_tiles : T_act - wb;
   const int64_t g_begin = wb + (Tw * blockIdx.x) / gridDim.x;
   const int64_t g_end = wb + (Tw * (blockIdx.x + 1)) / gridDim.x;
-  const int first_model = (int)(g_begin / p.tiles_per_model);
+  const int first_pos = (int)(g_begin / p.tiles_per_model);
   for (int64_t g = g_begin; g < g_end; ++g) {
-    const int model = (int)(g / p.tiles_per_model);
-    const int tile = (int)(g - (int64_t)model * p.tiles_per_model);
+    const int pos = (int)(g / p.tiles_per_model);
+    const int tile = (int)(g - (int64_t)pos * p.tiles_per_model);
+    const int model = p.sched ? p.sched[1 + pos] : pos;
     if (model != cur) {
       if (cur >= 0) flush();
       cur = model;
-      cur_slot = (size_t)wv * p.slots_per_wave + (size_t)(model - first_model);
+      cur_slot = (size_t)wv * p.slots_per_wave + (size_t)(pos - first_pos);
       md = p.models[model];
       sp.model = md.slot;
       iter = p.explicit_iter ? p.iter : md.st->iter;
@@ -745,14 +759,20 @@ constexpr int kReduceWarps = 8;
 
 __global__ void __launch_bounds__(32 * kReduceWarps)
     k_mp_reduce(const MpModel* __restrict__ models, const float* __restrict__ partial,
-                int part_stride, int slots, int n_mlp, int64_t w_off0, int64_t tpm, int64_t T,
-                int64_t G, int64_t wave_tiles, int models_per_wave, int slots_per_wave) {
+                int part_stride, int slots, int n_mlp, int64_t w_off0, int64_t tpm, int n_models,
+                const int32_t* __restrict__ sched, int64_t G, int64_t wave_tiles,
+                int models_per_wave, int slots_per_wave) {
   const int m = blockIdx.y;
+  // the model's position among the step's active models (k_mp_train numbers
+  // tiles over active models only); an inactive model has no partials
+  const int a = sched ? sched[1 + n_models + m] : m;
+  if (a < 0) return;
+  const int64_t T = (int64_t)(sched ? sched[0] : n_models) * tpm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * 32 + lane;
   // the model's wave and its tiles relative to the wave (tile counts stay
   // below 2^32 / G, so 32-bit products and quotients suffice)
-  const int wv = m / models_per_wave, m_rel = m - wv * models_per_wave;
+  const int wv = a / models_per_wave, m_rel = a - wv * models_per_wave;
   const int64_t wb = (int64_t)wv * wave_tiles;
   const uint32_t Tw = (uint32_t)(wave_tiles < T - wb ? wave_tiles : T - wb);
   const uint32_t G32 = (uint32_t)G, tpm32 = (uint32_t)tpm;
@@ -797,6 +817,44 @@ __global__ void __launch_bounds__(32 * kReduceWarps)
     else
       models[m].st->loss_sum = t;
   }
+}
+
+// The step's active models in index order (a block-wide exclusive scan of
+// model_active over the models): sched[0] = count, sched[1 + a] = index of the
+// a-th active model, sched[1 + n + m] = position of model m or -1. One block
+// of 1024 threads; launched before every grouped training step.
+__global__ void __launch_bounds__(1024) k_mp_schedule(const MpModel* __restrict__ models, int n,
+                                                      int32_t* __restrict__ sched) {
+  __shared__ int s_cnt[32];
+  __shared__ int s_total;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  int base = 0;
+  for (int c = 0; c < n; c += blockDim.x) {
+    const int m = c + tid;
+    const bool act = m < n && model_active(models[m].st);
+    const uint32_t b = __ballot_sync(0xffffffffu, act);
+    if (lane == 0) s_cnt[warp] = __popc(b);
+    __syncthreads();
+    if (warp == 0) {
+      const int v = lane < nw ? s_cnt[lane] : 0;
+      int x = v;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane < nw) s_cnt[lane] = x - v;  // exclusive prefix of the warps
+      if (lane == 31) s_total = x;
+    }
+    __syncthreads();
+    const int pos = base + s_cnt[warp] + __popc(b & ((1u << lane) - 1u));
+    if (m < n) {
+      sched[1 + n + m] = act ? pos : -1;
+      if (act) sched[1 + pos] = m;
+    }
+    base += s_total;
+    __syncthreads();
+  }
+  if (tid == 0) sched[0] = base;
 }
 
 // --------------------------------------------------------- decode kernel ---
@@ -1118,6 +1176,7 @@ struct MpCache {
   int graph_steps = 0;
   MpModel* d_models = nullptr;
   AdamModelPtrs* d_adam = nullptr;
+  int32_t* d_sched = nullptr;  // active-model schedule, 1 + 2 n ints
   float* d_partial = nullptr;
   size_t partial_cap = 0;
   cudaGraphExec_t exec = nullptr;
@@ -1125,11 +1184,13 @@ struct MpCache {
   cudaStream_t cap = nullptr;
   int models_per_wave = 0;
   int ctas_per_sm = 0;
+  bool scheduled = false;  // the captured graph launches k_mp_schedule
   void clear() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (d_models) cudaFree(d_models);
     if (d_adam) cudaFree(d_adam);
+    if (d_sched) cudaFree(d_sched);
     if (d_partial) cudaFree(d_partial);
     if (cap) cudaStreamDestroy(cap);
     d_partial = nullptr;
@@ -1138,6 +1199,7 @@ struct MpCache {
     graph = nullptr;
     d_models = nullptr;
     d_adam = nullptr;
+    d_sched = nullptr;
     cap = nullptr;
     models.clear();
     vols.clear();
@@ -1149,7 +1211,8 @@ bool same_cfg(const dvnr_train_cfg& a, const dvnr_train_cfg& b) {
   return a.lr == b.lr && a.beta1 == b.beta1 && a.beta2 == b.beta2 && a.eps == b.eps &&
          a.weight_decay == b.weight_decay && a.lambda_bnd == b.lambda_bnd &&
          a.sigma_bnd == b.sigma_bnd && a.batch == b.batch && a.loss == b.loss &&
-         a.growth_interval == b.growth_interval && a.seed == b.seed;
+         a.growth_interval == b.growth_interval && a.seed == b.seed &&
+         a.stop_loss == b.stop_loss && a.stop_decay == b.stop_decay;
 }
 
 MpParams base_params(const dvnr_model m, const MpLayout& lay, const dvnr_train_cfg* cfg) {
@@ -1220,6 +1283,11 @@ size_t partial_floats(const MpParams& p) {
 }
 
 dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStream_t s) {
+  if (p.sched) {
+    ProfScope ps("mp_schedule", s);
+    k_mp_schedule<<<1, 1024, 0, s>>>(p.models, n_models, const_cast<int32_t*>(p.sched));
+    DVNR_CUDA(cudaGetLastError());
+  }
   {
     ProfScope ps("train_fused_fp16", s);
     DVNR_WF_DISPATCH(W, F, launch_train_wf, p, train_grid(p), s);
@@ -1229,7 +1297,7 @@ dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStre
     ProfScope ps("mp_reduce", s);
     dim3 grid((unsigned)((p.n_mlp + 1 + 31) / 32), (unsigned)n_models);
     k_mp_reduce<<<grid, 32 * kReduceWarps, 0, s>>>(p.models, p.partial, p.part_stride, p.slots_per_cta, p.n_mlp,
-                                     p.w_off[0], p.tiles_per_model, p.total_tiles, train_grid(p),
+                                     p.w_off[0], p.tiles_per_model, n_models, p.sched, train_grid(p),
                                      p.wave_tiles, p.models_per_wave, p.slots_per_wave);
   }
   DVNR_CUDA(cudaGetLastError());
@@ -1355,7 +1423,7 @@ void mp_release(dvnr_model m) {
 }
 
 dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const dvnr_train_cfg* cfg,
-                     const AdamHyper& h, cudaStream_t s) {
+                     const AdamHyper& h, int64_t steps, bool uniform, cudaStream_t s) {
   dvnr_model m0 = models[0];
   MpLayout lay;
   if (!make_layout(m0, true, lay)) {
@@ -1379,6 +1447,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     }
     DVNR_CUDA(cudaMalloc(&c->d_models, sizeof(MpModel) * n));
     DVNR_CUDA(cudaMalloc(&c->d_adam, sizeof(AdamModelPtrs) * n));
+    DVNR_CUDA(cudaMalloc(&c->d_sched, sizeof(int32_t) * (1 + 2 * (size_t)n)));
     DVNR_CUDA(cudaMemcpy(c->d_models, hm.data(), sizeof(MpModel) * n, cudaMemcpyHostToDevice));
     DVNR_CUDA(cudaMemcpy(c->d_adam, ha.data(), sizeof(AdamModelPtrs) * n, cudaMemcpyHostToDevice));
     c->models.assign(models, models + n);
@@ -1387,6 +1456,10 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   MpParams p = base_params(m0, lay, cfg);
   p.total_tiles = (int64_t)p.tiles_per_model * n;
+  p.n_models = n;
+  // equal budgets and no stop rule: every model takes part in every step, so
+  // the schedule is the identity and its kernel is left out
+  p.sched = (uniform && cfg->stop_loss == 0.f) ? nullptr : c->d_sched;
   if (p.total_tiles * (int64_t)train_grid(p) >= (1LL << 32)) {
     set_error("FP16 path: %lld tiles per step is beyond the supported range", (long long)p.total_tiles);
     return DVNR_E_UNSUPPORTED;
@@ -1422,7 +1495,8 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
       set_waves(p, m0, n);
     }
   }
-  if (c->exec && (c->models_per_wave != p.models_per_wave || c->ctas_per_sm != p.lay.ctas_per_sm)) {
+  if (c->exec && (c->models_per_wave != p.models_per_wave || c->ctas_per_sm != p.lay.ctas_per_sm ||
+                  c->scheduled != (p.sched != nullptr))) {
     DVNR_CUDA(cudaStreamSynchronize(s));
     cudaGraphExecDestroy(c->exec);
     cudaGraphDestroy(c->graph);
@@ -1431,6 +1505,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   c->models_per_wave = p.models_per_wave;
   c->ctas_per_sm = p.lay.ctas_per_sm;
+  c->scheduled = p.sched != nullptr;
   const size_t need = partial_floats(p);
   if (c->partial_cap < need) {
     if (c->d_partial) {
@@ -1450,7 +1525,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     if (rc != DVNR_OK) return rc;
     return launch_adam(c->d_adam, n, m0->n_store, h, st);
   };
-  int64_t left = cfg->steps;
+  int64_t left = steps;
   if (profiling_on() || left < 8) {
     for (int64_t i = 0; i < left; ++i) {
       dvnr_status rc = one_step(s);
@@ -1483,7 +1558,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   while (left >= G) {
     DVNR_CUDA(cudaGraphLaunch(c->exec, s));
-    count_launches(3 * G);  // train, reduce, Adam per step
+    count_launches((p.sched ? 4 : 3) * G);  // [schedule,] train, reduce, Adam per step
     left -= G;
   }
   for (int64_t i = 0; i < left; ++i) {
@@ -1507,6 +1582,8 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
   DVNR_CUDA(cudaMemcpyAsync(d, &hm, sizeof(MpModel), cudaMemcpyHostToDevice, s));
   MpParams p = base_params(m, lay, cfg);
   p.total_tiles = p.tiles_per_model;
+  p.n_models = 1;
+  p.sched = nullptr;
   p.models = d;
   p.explicit_iter = 1;
   p.iter = iter;

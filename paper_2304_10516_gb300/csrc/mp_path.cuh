@@ -17,9 +17,12 @@ struct MpStepDebug {
 bool mp_supported(const dvnr_model m);
 // Free the FP16-path resources of a model (graphs, descriptor tables).
 void mp_release(dvnr_model m);
-// cfg->steps grouped steps of all n models (one fused kernel + Adam per step).
+// `steps` grouped steps of the n models (schedule, fused kernel, reduction,
+// Adam per step); a model leaves the steps once model_active is false.
+// `uniform`: every model's budget equals `steps` (with no stop rule the
+// schedule kernel is then skipped).
 dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const dvnr_train_cfg* cfg,
-                     const AdamHyper& h, cudaStream_t s);
+                     const AdamHyper& h, int64_t steps, bool uniform, cudaStream_t s);
 // One forward/backward of model slot 0 at iteration `iter` and loss scale S,
 // gradients left (scaled by S) in m->grad.
 dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* cfg, uint32_t iter,

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
                                                    int64_t n, AdamHyper h) {
   const AdamModelPtrs md = models[blockIdx.y];
   ModelState* st = md.st;
+  if (h.gated && !model_active(st)) return;  // budget spent or stopped: no work, no counters
   const bool skip = *((volatile uint32_t*)&st->overflow) != 0u;
   const float S = h.mixed ? st->loss_scale : 1.0f;
   const float inv_S = 1.0f / S;
@@ -237,7 +238,16 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
           }
         }
       }
-      st->last_loss = st->loss_sum * h.inv_batch;
+      const float L = st->loss_sum * h.inv_batch;
+      st->last_loss = L;
+      if (!skip) {
+        // moving average of the loss over the finite steps of the call and
+        // the early-stop test (Sec. 3.2)
+        const float e = st->loss_ema < 0.f ? L : __fadd_rn(__fmul_rn(h.stop_decay, st->loss_ema),
+                                                           __fmul_rn(1.0f - h.stop_decay, L));
+        st->loss_ema = e;
+        if (h.stop_loss > 0.f && e < h.stop_loss) st->stopped = 1u;
+      }
       st->loss_sum = 0.f;
       st->overflow = 0u;
       st->iter += 1u;
@@ -259,6 +269,18 @@ __global__ void k_state_reset(ModelState* st, float loss_scale) {
   st->loss_sum = 0.f;
   st->last_loss = 0.f;
   st->timeouts = 0u;
+  st->stop_at = 0xFFFFFFFFu;
+  st->loss_ema = -1.f;
+  st->stopped = 0u;
+}
+
+// Start of a training call: the budget runs from the current iteration (the
+// end saturates at 2^32 - 1) and the moving average starts afresh.
+__global__ void k_begin_call(ModelState* st, uint32_t budget) {
+  const uint32_t it = st->iter;
+  st->stop_at = budget > 0xFFFFFFFFu - it ? 0xFFFFFFFFu : it + budget;
+  st->loss_ema = -1.f;
+  st->stopped = 0u;
 }
 
 // Hand out the gradient of one forward/backward without an optimiser step:
@@ -362,6 +384,15 @@ dvnr_status launch_widen_half(dvnr_model m, cudaStream_t s) {
   {
     ProfScope ps_("widen_half", s);
     k_widen_half<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(m->theta16, m->theta, m->n_store);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_begin_call(ModelState* st, uint32_t budget, cudaStream_t s) {
+  {
+    ProfScope ps_("begin_call", s);
+    k_begin_call<<<1, 1, 0, s>>>(st, budget);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;

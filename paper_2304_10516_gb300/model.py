@@ -46,11 +46,17 @@ class TrainConfig:
     loss: int = A.DVNR_LOSS_L1
     growth_interval: int = 2000
     seed: int = 0
+    # Sec. 3.2 iteration budget and early stop (see dvnr_train_cfg)
+    epochs: int = 0
+    min_steps: int = 0
+    stop_loss: float = 0.0
+    stop_decay: float = 0.9
 
     def to_c(self) -> A.dvnr_train_cfg:
         return A.dvnr_train_cfg(self.lr, self.beta1, self.beta2, self.eps, self.weight_decay,
                                 self.lambda_bnd, self.sigma_bnd, self.batch, self.precision,
-                                self.loss, self.growth_interval, self.steps, self.seed)
+                                self.loss, self.growth_interval, self.steps, self.seed,
+                                self.epochs, self.min_steps, self.stop_loss, self.stop_decay)
 
 
 def _ptr(t):

@@ -546,3 +546,104 @@ def test_training_reduces_error(orc):
     assert st.adam_t == 150 and st.iter == 150
     assert hist[-10:].mean() < 0.5 * hist[:10].mean()
     assert e1 < 0.1 * e0
+
+
+# ------------------------------------------- iteration budget, early stop ----
+def test_max_iterations_counts_batches_by_brute_force(orc):
+    # Sec. 3.2: N_train^max = max(N_min, ceil(N_vox / N_batch) N_epoch); the
+    # batch count is checked by covering the voxels one batch at a time
+    for n_vox in (1, 4095, 4096, 4097, 64 ** 3, 96 * 97 * 98, 160 ** 3):
+        for batch in (1, 4096, 16384):
+            k, covered = 0, 0
+            while covered < n_vox:
+                covered += batch
+                k += 1
+            for epochs in (1, 16):
+                assert orc.max_iterations(n_vox, batch, epochs=epochs) == k * epochs
+                assert orc.max_iterations(n_vox, batch, epochs=epochs, min_steps=k * epochs + 7) \
+                    == k * epochs + 7
+    # the 64^3 workload at batch 4096 and 16 epochs: 64 batches per epoch
+    assert orc.max_iterations(64 ** 3, 4096, epochs=16) == 1024
+    # epochs = 0 keeps the fixed count, still raised to N_min
+    assert orc.max_iterations(10 ** 6, 4096, steps=300) == 300
+    assert orc.max_iterations(10 ** 6, 4096, steps=300, min_steps=500) == 500
+    assert orc.max_iterations(10 ** 6, 4096, steps=0) == 0
+
+
+def test_stop_rule_matches_geometric_closed_form(orc):
+    # losses L_t = r^t (t = 1, 2, ...): the moving average m_1 = L_1,
+    # m_t = d m_{t-1} + (1 - d) L_t has the closed form
+    # m_t = d^(t-1) r + (1 - d) r^t (1 - (d/r)^(t-1)) / (1 - d/r)
+    r, d = 0.97, 0.9
+    n = 400
+    L = r ** np.arange(1, n + 1, dtype=np.float64)
+
+    def closed(t):
+        q = d / r
+        return d ** (t - 1) * r + (1 - d) * r ** t * (1 - q ** (t - 1)) / (1 - q)
+
+    for t in (1, 2, 5, 50, 400):
+        steps, ema = orc.stop_step(L[:t], d, 0.0)
+        assert steps == t
+        assert abs(ema - closed(t)) <= 1e-12 * closed(t)
+    # the first t with m_t below a threshold between two consecutive values
+    thr = 0.5 * (closed(120) + closed(121))
+    steps, ema = orc.stop_step(L, d, thr)
+    assert steps == 121 and abs(ema - closed(121)) <= 1e-12
+    # no threshold: the whole sequence; threshold above L_1: stop after step 1
+    assert orc.stop_step(L, d, 0.0)[0] == n
+    assert orc.stop_step(L, d, 1.0)[0] == 1
+
+
+def test_stop_rule_skips_nonfinite_steps(orc):
+    # a skipped (non-finite) step counts against the budget but leaves the
+    # average as it was: the average of the finite steps alone, one step later
+    L = np.array([1.0, np.inf, 0.5, np.nan, 0.2, 0.1])
+    fin = np.array([1, 0, 1, 0, 1, 1], dtype=np.int32)
+    d = 0.5
+    steps, ema = orc.stop_step(L, d, 0.0, finite=fin)
+    m = 1.0
+    for x in (0.5, 0.2, 0.1):
+        m = d * m + (1 - d) * x
+    assert steps == 6 and ema == pytest.approx(m, rel=1e-15)
+    # threshold crossed at the 5th step (m = 0.45 after 0.2)
+    steps, _ = orc.stop_step(L, d, 0.5, finite=fin)
+    assert steps == 5
+    # an all-skipped call has no average
+    assert orc.stop_step(L[1:2], d, 0.3, finite=fin[1:2]) == (1, -1.0)
+
+
+def test_train_budget_is_train_stopped_at_the_rule(orc):
+    # training under a budget is plain training of the same number of steps,
+    # and with a threshold it stops where the rule applied to the full loss
+    # history says
+    from paper_2304_10516_gb300 import volumes
+
+    vol = volumes.blobs(16, seed=1001)
+    cfg = orc.Config(4, 2, 10, 4, 1.5, 16, 2)
+    vmin, vmax = float(vol.min()), float(vol.max())
+    tc = orc.TrainConfig(batch=256, lr=1e-2, seed=5)
+
+    def fresh():
+        th = orc.init_params(cfg, 2)
+        return th, np.zeros_like(th), np.zeros_like(th), orc.State()
+
+    th, m1, m2, st = fresh()
+    full = orc.train(cfg, tc, st, th, m1, m2, vol, vmin, vmax, 60)
+    th_b, m1_b, m2_b, st_b = fresh()
+    n, hist, _, stopped = orc.train_budget(cfg, tc, st_b, th_b, m1_b, m2_b, vol, vmin, vmax, 60)
+    assert n == 60 and not stopped and st_b.iter == 60
+    # (the oracle's threaded loss sum may round differently in the last bit)
+    np.testing.assert_allclose(hist, full, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(th_b, th, rtol=1e-9, atol=1e-15)
+    thr = float(np.median(full))
+    want, want_ema = orc.stop_step(full, 0.9, thr)
+    assert want < 60
+    th_s, m1_s, m2_s, st_s = fresh()
+    n, hist, ema, stopped = orc.train_budget(cfg, tc, st_s, th_s, m1_s, m2_s, vol, vmin, vmax, 60,
+                                             stop_loss=thr, decay=0.9)
+    assert stopped and n == want and st_s.iter == want
+    assert ema == pytest.approx(want_ema, rel=1e-12)
+    th_r, m1_r, m2_r, st_r = fresh()
+    orc.train(cfg, tc, st_r, th_r, m1_r, m2_r, vol, vmin, vmax, want)
+    np.testing.assert_allclose(th_s, th_r, rtol=1e-9, atol=1e-15)
