@@ -273,6 +273,8 @@ def run_ours(args, rank, world, local_rank):
     result["render"] = {"value": 1024 * 1024 * 512 / (tms.value / 1e3), "unit": "ray samples/s",
                         "march_ms": tms.value, "decode_plus_march_ms": r0.elapsed_time(r1),
                         "image": [1024, 1024], "samples_per_ray": 512}
+    # ---- the same frame marched through the network itself (no decoded grid)
+    result["render_inr"] = render_inr_leg(model, tf, img, out, stream)
 
     # ---- end to end through the public API: host volume -> train -> loss
     pinned = torch.from_numpy(vol_np).pin_memory()
@@ -567,6 +569,34 @@ def run_insitu(args, rank, world, local_rank):
         "per_step": per,
     }
     return res
+
+
+def render_inr_leg(model, tf, img_grid, grid, stream):
+    """Direct INR ray-march of the benchmark frame: time, image PSNR against
+    the decoded-grid march and the device memory each needs beyond the
+    model (decoded grid vs per-segment composites)."""
+    import torch
+
+    from paper_2304_10516_gb300 import model as dv
+
+    w = h = 1024
+    spr = 512
+    img = dv.render_inr([model], tf, w, h, spr)
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        dv.render_inr([model], tf, w, h, spr, out=img)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    mse = float(((img - img_grid) ** 2).mean())
+    return {"value": w * h * spr / (ms / 1e3), "unit": "ray samples/s (network inferences/s)",
+            "ms": ms, "psnr_vs_grid_march_db": 10 * math.log10(1.0 / max(mse, 1e-30)),
+            "max_abs_vs_grid_march": float((img - img_grid).abs().max()),
+            "work_bytes": w * h * 16, "grid_bytes": grid.numel() * 4,
+            "model_bytes_fp16": model.n_params * 2}
 
 
 def adaptive_budget(models, vols, boxes, enc, mlp, w, rank):

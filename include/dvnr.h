@@ -278,6 +278,24 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf,
                         int32_t w, int32_t h, int32_t spr, float* rgba_dev,
                         void* stream);
 
+/* Direct volume rendering from the networks (Sec. 4.3: the renderer infers
+ * the models at the ray samples instead of decoding them to grids, keeping
+ * the memory footprint of the compressed form). Camera, samples, transfer
+ * function and compositing as dvnr_render; the value of a sample is its
+ * block's network evaluated at the sample position (mapped into the block's
+ * unit domain and clamped to it, as dvnr_decode_points), de-normalised. The
+ * boxes must not overlap. All models must use one precision (the training
+ * precision, or dvnr_set_precision); FP16 models must also share encoding
+ * and MLP configuration. Work memory: 16 bytes per (pixel, block) pair whose
+ * ray crosses the block (FP32 models: plus 16 bytes per sample of a chunk
+ * of at most 2^24 samples), allocated stream-ordered and released before
+ * return. Synchronises the stream. Errors: DVNR_E_INVALID
+ * (arguments, mixed precisions or configurations), DVNR_E_UNSUPPORTED,
+ * DVNR_E_CUDA.                                                               */
+dvnr_status dvnr_render_inr(const dvnr_model* models, int32_t n, const dvnr_tf* tf,
+                            int32_t w, int32_t h, int32_t spr, float* rgba_dev,
+                            void* stream);
+
 /* FP64 reduction of the reconstruction error between two float32 arrays
  * (Sec. 5: PSNR from the mean squared error): out_host[0] = sum of squared
  * differences, out_host[1] = max absolute difference. Synchronises.       */

@@ -153,6 +153,19 @@ void orc_render(int32_t n_blocks, const double* const* grids,
                 const int64_t* lo, const int64_t* hi, const double* tf,
                 int32_t w, int32_t h, int32_t spr, double* rgba);
 
+/* Direct volume rendering from the networks (Sec. 4.3): the camera, samples,
+ * transfer function and compositing of orc_render, with the value of a
+ * sample taken from its block's network at the sample position (global
+ * voxel coordinates mapped to the block's unit domain, clamped, rounded to
+ * the 2^-24 lattice) and de-normalised with the block's value range. Only
+ * the n_pix pixels listed in pix (index py * w + px) are rendered, into
+ * rgba[4 i ...]. thetas/vmin/vmax/ghost per block; one configuration.    */
+void orc_render_inr(const orc_cfg* c, int32_t n_blocks, const double* const* thetas,
+                    const int64_t* lo, const int64_t* hi, const int32_t* ghost,
+                    int mixed, const double* vmin, const double* vmax,
+                    const double* tf, int32_t w, int32_t h, int32_t spr,
+                    int64_t n_pix, const int64_t* pix, double* rgba);
+
 double orc_mse(const double* a, const float* b, int64_t n, double* max_abs);
 
 int  orc_threads(void);

@@ -125,6 +125,9 @@ def _lib_handle():
                                             C.c_double, C.c_double, _P]
             lib.orc_render.argtypes = [C.c_int32, _P, _P, _P, _P, C.c_int32, C.c_int32,
                                        C.c_int32, _P]
+            lib.orc_render_inr.argtypes = [C.POINTER(_Cfg), C.c_int32, _P, _P, _P, _P, C.c_int,
+                                           _P, _P, _P, C.c_int32, C.c_int32, C.c_int32,
+                                           C.c_int64, _P, _P]
             lib.orc_mse.argtypes = [_P, _P, C.c_int64, _P]
             lib.orc_mse.restype = C.c_double
             lib.orc_threads.restype = C.c_int
@@ -368,6 +371,28 @@ def render(grids, lo, hi, tf, w, h, spr):
     _lib_handle().orc_render(len(gs), C.cast(ptrs, C.c_void_p), _ptr(lo_a), _ptr(hi_a), _ptr(tf_a),
                              w, h, spr, _ptr(out))
     return out
+
+
+def render_inr(cfg: Config, thetas, lo, hi, ghost, vmin, vmax, tf, w, h, spr, pixels=None,
+               mixed=False):
+    """Ray-march the networks of the blocks directly (Sec. 4.3 reading, the
+    conventions of `render`). pixels: indices py * w + px (all if None).
+    Returns (h, w, 4) for the whole image, else (len(pixels), 4)."""
+    ths = [_arr(t, np.float64) for t in thetas]
+    nb = len(ths)
+    ptrs = (C.c_void_p * nb)(*[t.ctypes.data for t in ths])
+    lo_a = _arr(lo, np.int64).reshape(-1, 3)
+    hi_a = _arr(hi, np.int64).reshape(-1, 3)
+    g = _arr(np.broadcast_to(np.asarray(ghost), (nb,)), np.int32)
+    vmn = _arr(np.broadcast_to(np.asarray(vmin, dtype=np.float64), (nb,)), np.float64)
+    vmx = _arr(np.broadcast_to(np.asarray(vmax, dtype=np.float64), (nb,)), np.float64)
+    pix = _arr(np.arange(w * h) if pixels is None else pixels, np.int64)
+    out = np.zeros((pix.size, 4), dtype=np.float64)
+    tfa = _arr(tf, np.float64)
+    _lib_handle().orc_render_inr(cfg.ref, nb, C.cast(ptrs, C.c_void_p), _ptr(lo_a), _ptr(hi_a),
+                                 _ptr(g), int(mixed), _ptr(vmn), _ptr(vmx), _ptr(tfa), w, h, spr,
+                                 pix.size, _ptr(pix), _ptr(out))
+    return out.reshape(h, w, 4) if pixels is None else out
 
 
 def mse(a, b):

@@ -28,7 +28,7 @@ EXPORTS = [
     "dvnr_get_state", "dvnr_train", "dvnr_train_grad", "dvnr_decode_points", "dvnr_decode_grid",
     "dvnr_render", "dvnr_error_stats", "dvnr_corner_indices", "dvnr_profile_enable",
     "dvnr_profile_read", "dvnr_launch_count", "dvnr_selftest_umma",
-    "dvnr_error_stats_noalloc", "dvnr_export_fp16", "dvnr_import_fp16",
+    "dvnr_error_stats_noalloc", "dvnr_export_fp16", "dvnr_import_fp16", "dvnr_render_inr",
 ]
 
 
@@ -99,6 +99,8 @@ _SIGS = {
     "dvnr_decode_grid": ([_P, _P, _P], C.c_int),
     "dvnr_render": ([_P, C.c_int32, C.POINTER(dvnr_tf), C.c_int32, C.c_int32, C.c_int32, _P, _P],
                     C.c_int),
+    "dvnr_render_inr": ([_P, C.c_int32, C.POINTER(dvnr_tf), C.c_int32, C.c_int32, C.c_int32, _P,
+                         _P], C.c_int),
     "dvnr_error_stats": ([_P, _P, C.c_int64, _P, _P], C.c_int),
     "dvnr_corner_indices": ([_P, _P, C.c_int64, _P, _P], C.c_int),
     "dvnr_profile_enable": ([C.c_int32], C.c_int),

@@ -674,6 +674,28 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, 
   return rc;
 }
 
+dvnr_status dvnr_render_inr(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w,
+                            int32_t h, int32_t spr, float* rgba_dev, void* stream) {
+  g_err[0] = 0;
+  if (n < 1 || !models || !tf || !rgba_dev) return fail(DVNR_E_INVALID, "NULL argument or n < 1");
+  if (w < 1 || h < 1 || spr < 1) return fail(DVNR_E_INVALID, "w, h, spr must be >= 1");
+  for (int i = 0; i < n; ++i) {
+    if (!models[i]) return fail(DVNR_E_INVALID, "model %d is NULL", i);
+    if (models[i]->device != models[0]->device) return fail(DVNR_E_INVALID, "models on different devices");
+    if (models[i]->precision != models[0]->precision)
+      return fail(DVNR_E_INVALID, "model %d: all models must use one precision", i);
+    if (models[0]->precision == DVNR_FP16) {
+      if (!same_arch(models[i], models[0]))
+        return fail(DVNR_E_INVALID, "FP16 rendering needs one configuration for all models");
+      if (!mp_supported(models[i]))
+        return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+    }
+  }
+  dvnr_status rc = use_device(models[0]);
+  if (rc != DVNR_OK) return rc;
+  return render_inr(models, n, *tf, w, h, spr, rgba_dev, (cudaStream_t)stream);
+}
+
 dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n, double* out_host,
                              void* stream) {
   if (!out_host || n < 0 || (n > 0 && (!a_dev || !b_dev))) return fail(DVNR_E_INVALID, "bad argument");

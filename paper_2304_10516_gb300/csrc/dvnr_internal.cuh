@@ -347,6 +347,11 @@ struct RenderBlock {
 dvnr_status launch_render(const RenderBlock* blocks_dev, int n_blocks, const float lo[3],
                           const float hi[3], const dvnr_tf& tf, int w, int h, int spr,
                           float* rgba, cudaStream_t s);
+// Direct INR ray-marching (render_inr.cu): same camera and transfer function
+// as launch_render, values from the models' networks at the ray samples.
+// All models share one precision; FP16 models also one architecture.
+dvnr_status render_inr(const dvnr_model* models, int n, const dvnr_tf& tf, int w, int h, int spr,
+                       float* rgba, cudaStream_t s);
 dvnr_status launch_state_reset(ModelState* st, float loss_scale, cudaStream_t s);
 dvnr_status launch_state_reset_scale(ModelState* st, float loss_scale, cudaStream_t s);
 dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_batch, float* grad_out,

@@ -31,35 +31,16 @@
 #include <string>
 #include <vector>
 
+#include "mp_common.cuh"
 #include "mp_path.cuh"
-#include "umma.cuh"
 
 namespace dvnr {
 
 namespace {
 
-constexpr int kTile = 128;
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
 [[maybe_unused]] constexpr int kTrainKernelRevision = 7;
-#ifndef DVNR_DEC_PAIR
-#define DVNR_DEC_PAIR false
-#endif
-#ifndef DVNR_DEC_GROUP
-#define DVNR_DEC_GROUP 4
-#endif
-#ifndef DVNR_TRAIN_PAIR
-#define DVNR_TRAIN_PAIR true
-#endif
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s of SM clock per wait
-
-__device__ __forceinline__ uint32_t tile_off(uint32_t f, uint32_t s) {
-  return ((((f >> 3) << 4) + (s >> 3)) << 7) + ((s & 7u) << 4) + ((f & 7u) << 1);
-}
-// Weight (out o, in i) of a layer with `out` rows: core matrix (o/8, i/8).
-__device__ __forceinline__ uint32_t wsm_off(uint32_t o, uint32_t i, uint32_t out) {
-  return (((i >> 3) * (out >> 3) + (o >> 3)) << 7) + ((o & 7u) << 4) + ((i & 7u) << 1);
-}
 
 struct MpModel {
   const __half* theta16;
@@ -68,15 +49,6 @@ struct MpModel {
   int32_t nx, ny, nz;
   uint32_t slot;
   ModelState* st;
-};
-
-struct MpLayout {
-  uint32_t smem_wout, smem_w, smem_dz, smem_act, smem_bytes;
-  uint32_t wbyte[kMaxHidden + 1];   // byte offset of W_k inside the weight area
-  uint32_t act_off[kMaxHidden];     // feature offset of H_k in ACT (H_0 = X0)
-  uint32_t tmem_cols;
-  uint32_t dw_col[kMaxHidden];      // TMEM column of dW_k
-  int ctas_per_sm;
 };
 
 struct MpParams {
@@ -128,178 +100,6 @@ struct MpDecodeParams {
   float* out;
 };
 
-// ---------------------------------------------------------------- gathers --
-template <int F>
-struct HalfVec;
-template <>
-struct HalfVec<1> {
-  static __device__ __forceinline__ void load(const __half* p, float* v) { v[0] = __half2float(__ldg(p)); }
-};
-template <>
-struct HalfVec<2> {
-  static __device__ __forceinline__ void load(const __half* p, float* v) {
-    const __half2 a = __ldg(reinterpret_cast<const __half2*>(p));
-    const float2 f = __half22float2(a);
-    v[0] = f.x;
-    v[1] = f.y;
-  }
-};
-template <>
-struct HalfVec<4> {
-  static __device__ __forceinline__ void load(const __half* p, float* v) {
-    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
-    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-  }
-};
-template <>
-struct HalfVec<8> {
-  static __device__ __forceinline__ void load(const __half* p, float* v) {
-    HalfVec<4>::load(p, v);
-    HalfVec<4>::load(p + 4, v + 4);
-  }
-};
-
-template <int F>
-__device__ __forceinline__ void red_add(float* p, const float* g);
-template <>
-__device__ __forceinline__ void red_add<1>(float* p, const float* g) {
-  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(g[0]) : "memory");
-}
-template <>
-__device__ __forceinline__ void red_add<2>(float* p, const float* g) {
-  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(g[0]), "f"(g[1]) : "memory");
-}
-template <>
-__device__ __forceinline__ void red_add<4>(float* p, const float* g) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(g[0]), "f"(g[1]),
-               "f"(g[2]), "f"(g[3])
-               : "memory");
-}
-template <>
-__device__ __forceinline__ void red_add<8>(float* p, const float* g) {
-  red_add<4>(p, g);
-  red_add<4>(p + 4, g + 4);
-}
-
-// Store F halves of one sample row (features f0 .. f0+F-1, same 16-byte row).
-template <int F>
-__device__ __forceinline__ void st_row(uint8_t* base, uint32_t off, const float* v) {
-  if (F == 1) {
-    *reinterpret_cast<__half*>(base + off) = __float2half_rn(v[0]);
-  } else if (F == 2) {
-    *reinterpret_cast<__half2*>(base + off) = __floats2half2_rn(v[0], v[1]);
-  } else if (F == 4) {
-    uint2 u;
-    __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-    u.x = *reinterpret_cast<uint32_t*>(&a);
-    u.y = *reinterpret_cast<uint32_t*>(&b);
-    *reinterpret_cast<uint2*>(base + off) = u;
-  } else {
-    uint4 u;
-    __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-    __half2 c = __floats2half2_rn(v[4], v[5]), d = __floats2half2_rn(v[6], v[7]);
-    u.x = *reinterpret_cast<uint32_t*>(&a);
-    u.y = *reinterpret_cast<uint32_t*>(&b);
-    u.z = *reinterpret_cast<uint32_t*>(&c);
-    u.w = *reinterpret_cast<uint32_t*>(&d);
-    *reinterpret_cast<uint4*>(base + off) = u;
-  }
-}
-
-// Hash-grid encoding of one coordinate, FP16 tables, FP32 interpolation,
-// written as FP16 to the sample's row of the ACT tile (feature 0 .. D-1).
-// The corner loads of LG levels are issued together so that their latencies
-// overlap; with PAIR, x-neighbour corners in an aligned entry pair share one
-// load (training samples are scattered, so this saves requests; decoding walks
-// the grid in x order, where neighbouring lanes already share lines).
-constexpr int kLevelGroup = 4;
-
-template <int F, bool PAIR = true, int LG = kLevelGroup>
-__device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half* __restrict__ tab16,
-                                               uint3 m, bool valid, uint8_t* act, uint32_t s) {
-  for (int l0 = 0; l0 < lv.L; l0 += LG) {
-    float v[LG][8][F];
-    float fr[LG][3];
-#pragma unroll
-    for (int g = 0; g < LG; ++g) {
-      const int l = l0 + g;
-      const bool on = valid && l < lv.L;
-      uint32_t bx = 0, by = 0, bz = 0;
-      fr[g][0] = fr[g][1] = fr[g][2] = 0.f;
-      if (on) {
-        lattice(m.x, lv.N[l], bx, fr[g][0]);
-        lattice(m.y, lv.N[l], by, fr[g][1]);
-        lattice(m.z, lv.N[l], bz, fr[g][2]);
-      }
-      if constexpr (PAIR && F <= 2) {
-        // corners x and x+1 whose entries form an aligned pair {2j, 2j+1}
-        // (every even x on a hashed level, every even index on a dense one)
-        // come in one load of both entries
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (on) {
-            const uint32_t y = by + (q & 1), z = bz + (q >> 1);
-            const uint32_t i0 = corner_index(lv, l, bx, y, z);
-            const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
-            const __half* tab = tab16 + lv.off[l];
-            if (i1 == (i0 ^ 1u)) {
-              float both[2 * F];
-              HalfVec<2 * F>::load(tab + (size_t)(i0 & ~1u) * F, both);
-              const bool odd = (i0 & 1u) != 0u;  // corner x is the upper entry
-#pragma unroll
-              for (int f = 0; f < F; ++f) {
-                v[g][2 * q][f] = odd ? both[F + f] : both[f];
-                v[g][2 * q + 1][f] = odd ? both[f] : both[F + f];
-              }
-            } else {
-              HalfVec<F>::load(tab + (size_t)i0 * F, v[g][2 * q]);
-              HalfVec<F>::load(tab + (size_t)i1 * F, v[g][2 * q + 1]);
-            }
-          } else {
-#pragma unroll
-            for (int f = 0; f < F; ++f) v[g][2 * q][f] = v[g][2 * q + 1][f] = 0.f;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          if (on) {
-            const uint32_t idx =
-                corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
-            HalfVec<F>::load(tab16 + lv.off[l] + (size_t)idx * F, v[g][k]);
-          } else {
-#pragma unroll
-            for (int f = 0; f < F; ++f) v[g][k][f] = 0.f;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < LG; ++g) {
-      const int l = l0 + g;
-      if (l >= lv.L) break;
-      const float fx = fr[g][0], fy = fr[g][1], fz = fr[g][2];
-      float acc[F];
-#pragma unroll
-      for (int f = 0; f < F; ++f) acc[f] = 0.f;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
-                        (((k >> 2) & 1) ? fz : 1.f - fz);
-#pragma unroll
-        for (int f = 0; f < F; ++f) acc[f] += w * v[g][k][f];
-      }
-      st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
-    }
-  }
-}
-
-// Backward of the encoding: dL/d(encoding) is read from TMEM (16 columns
-// at a time, the warp-collective load runs on every lane) and each level's
-// gradient times the trilinear weights is added to its 8 corner entries
-// with vector reductions. Returns true if a non-finite value was seen.
 template <int F>
 __device__ __forceinline__ bool scatter_from_tmem(const LevelTab& lv, float* __restrict__ grad,
                                                   uint3 m, bool valid, uint32_t tl,
@@ -372,38 +172,6 @@ __device__ __forceinline__ bool scatter_from_tmem(const LevelTab& lv, float* __r
     }
   }
   return bad;
-}
-
-// Load one model's FP16 weights into the core-matrix weight area and w_out
-// (as FP32) into s_wout.
-__device__ void load_weights(const __half* __restrict__ theta16, const int64_t* w_off, int D, int H,
-                             int W, const MpLayout& lay, uint8_t* smem) {
-  uint8_t* s_w = smem + lay.smem_w;
-  float* s_wout = reinterpret_cast<float*>(smem + lay.smem_wout);
-  for (int k = 0; k < H; ++k) {
-    const int in = k == 0 ? D : W;
-    const __half* src = theta16 + w_off[k];
-    uint8_t* dst = s_w + lay.wbyte[k];
-    for (int e = threadIdx.x; e < W * in; e += blockDim.x) {
-      const int o = e / in, i = e - o * in;
-      *reinterpret_cast<__half*>(dst + wsm_off(o, i, W)) = src[e];
-    }
-  }
-  for (int j = threadIdx.x; j < W; j += blockDim.x) s_wout[j] = __half2float(theta16[w_off[H] + j]);
-}
-
-// Forward MMA chain of layer k: scratch[0:W) = ACT(k) x W_k^T.
-__device__ __forceinline__ void issue_forward(uint32_t tmem, const uint8_t* smem, const MpLayout& lay,
-                                              int k, int in, int W) {
-  const uint32_t a0 = umma::smem_u32(smem + lay.smem_act) + (lay.act_off[k] >> 3) * 2048u;
-  const uint32_t b0 = umma::smem_u32(smem + lay.smem_w + lay.wbyte[k]);
-  const uint32_t id = umma::idesc_f16(kTile, W, 0, 0);
-  const uint32_t wb = (uint32_t)(W >> 3) * 128u;
-  for (int kk = 0; kk < in / 16; ++kk) {
-    const uint64_t a = umma::sdesc(a0 + kk * 4096u, 2048u, 128u);
-    const uint64_t b = umma::sdesc(b0 + kk * 2u * wb, wb, 128u);
-    umma::mma_f16(tmem, a, b, id, kk > 0);
-  }
 }
 
 // ------------------------------------------------------- training kernel ---
@@ -858,17 +626,6 @@ __global__ void __launch_bounds__(1024) k_mp_schedule(const MpModel* __restrict_
 }
 
 // --------------------------------------------------------- decode kernel ---
-__device__ __forceinline__ uint32_t dec_unit_to_fixed(float g, float origin, int64_t n) {
-  if (n < 2) return 0u;
-  float u = (g - origin) / (float)(n - 1);
-  u = fminf(fmaxf(u, 0.f), 1.f);
-  return (uint32_t)__float2uint_rn(u * 16777216.0f);
-}
-__device__ __forceinline__ uint32_t dec_grid_fixed(int64_t j, int64_t n) {
-  if (n < 2) return 0u;
-  return (uint32_t)((2 * j * (int64_t)kFixOne + (n - 1)) / (2 * (n - 1)));
-}
-
 template <int W, int F>
 __global__ void __launch_bounds__(kTile) k_mp_decode(const __grid_constant__ MpDecodeParams p) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -1070,69 +827,6 @@ __global__ void __launch_bounds__(128) k_umma_selftest(int32_t* mismatches) {
 }
 
 // ----------------------------------------------------------- host side -----
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
-
-uint32_t pow2_cols(uint32_t c) {
-  uint32_t p2 = 32;
-  while (p2 < c) p2 <<= 1;
-  return p2;
-}
-
-bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
-  const int W = m->mlp.width, H = m->mlp.n_hidden, D = m->lv.in_dim;
-  lay = MpLayout{};
-  uint32_t off = 64;  // mbarrier, TMEM slot, abort flag, spare
-  lay.smem_wout = off;
-  off += 64 * 4;
-  off = (off + 127) / 128 * 128;
-  lay.smem_w = off;
-  uint32_t wb = 0;
-  for (int k = 0; k < H; ++k) {
-    lay.wbyte[k] = wb;
-    wb += (uint32_t)W * (k == 0 ? D : W) * 2;
-  }
-  off += wb;
-  off = (off + 1023) / 1024 * 1024;
-  const uint32_t feat_bytes = 2048 / 8;  // one feature across 128 samples, per 8-feature group
-  if (train) {
-    lay.smem_dz = off;
-    off += (uint32_t)H * W * feat_bytes;
-  }
-  lay.smem_act = off;
-  lay.act_off[0] = 0;
-  for (int k = 1; k < H; ++k) lay.act_off[k] = (uint32_t)D + (uint32_t)(k - 1) * W;
-  off += ((uint32_t)D + (uint32_t)(H - 1) * W) * feat_bytes;
-  if (train) {
-    // the weight-gradient product of dZ_H reads 128 features from its start
-    const uint32_t need = lay.smem_dz + ((uint32_t)(H - 1) * W + 128) * feat_bytes;
-    off = std::max(off, need);
-  }
-  lay.smem_bytes = (off + 1023) / 1024 * 1024;
-  const uint32_t scratch = (uint32_t)std::max(W, D);
-  uint32_t col = scratch;
-  if (train) {
-    for (int k = 0; k < H; ++k) {
-      lay.dw_col[k] = col;
-      col += (uint32_t)(k == 0 ? D : W);
-    }
-  }
-  lay.tmem_cols = pow2_cols(col);
-  if (lay.tmem_cols > 512 || lay.smem_bytes > 227 * 1024) return false;
-  const int by_smem = (int)((228 * 1024) / (lay.smem_bytes + 1024));
-  const int by_tmem = (int)(512 / lay.tmem_cols);
-  lay.ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_tmem), train ? 2 : 4));
-  return true;
-}
-
 template <int W, int F>
 void set_smem_attr(bool train, uint32_t bytes) {
   if (train)
@@ -1150,22 +844,6 @@ void launch_decode_wf(const MpDecodeParams& p, int grid, cudaStream_t s) {
   k_mp_decode<W, F><<<grid, kTile, p.lay.smem_bytes, s>>>(p);
 }
 
-#define DVNR_WF_DISPATCH(W, F, FN, ...)                         \
-  do {                                                          \
-    const int w_ = (W), f_ = (F);                               \
-    if (w_ == 16 && f_ == 1) FN<16, 1>(__VA_ARGS__);            \
-    else if (w_ == 16 && f_ == 2) FN<16, 2>(__VA_ARGS__);       \
-    else if (w_ == 16 && f_ == 4) FN<16, 4>(__VA_ARGS__);       \
-    else if (w_ == 16 && f_ == 8) FN<16, 8>(__VA_ARGS__);       \
-    else if (w_ == 32 && f_ == 1) FN<32, 1>(__VA_ARGS__);       \
-    else if (w_ == 32 && f_ == 2) FN<32, 2>(__VA_ARGS__);       \
-    else if (w_ == 32 && f_ == 4) FN<32, 4>(__VA_ARGS__);       \
-    else if (w_ == 32 && f_ == 8) FN<32, 8>(__VA_ARGS__);       \
-    else if (w_ == 64 && f_ == 1) FN<64, 1>(__VA_ARGS__);       \
-    else if (w_ == 64 && f_ == 2) FN<64, 2>(__VA_ARGS__);       \
-    else if (w_ == 64 && f_ == 4) FN<64, 4>(__VA_ARGS__);       \
-    else if (w_ == 64 && f_ == 8) FN<64, 8>(__VA_ARGS__);       \
-  } while (0)
 
 // Per-model cache of the FP16 path: device tables of the last grouped call
 // and its captured CUDA graph.

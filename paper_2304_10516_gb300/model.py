@@ -226,6 +226,20 @@ def render(models, tf, w, h, spr, out=None, stream=None):
     return out
 
 
+def render_inr(models, tf, w, h, spr, out=None, stream=None):
+    """Ray-march the networks directly (no decoded grids); same image
+    conventions as `render`."""
+    import torch
+
+    n = len(models)
+    hs = (C.c_void_p * n)(*[m.handle for m in models])
+    if out is None:
+        out = torch.empty((h, w, 4), dtype=torch.float32, device="cuda")
+    A.call("dvnr_render_inr", C.cast(hs, C.c_void_p), n, C.byref(tf), w, h, spr, _ptr(out),
+           _stream(stream))
+    return out
+
+
 def error_stats(a, b, stream=None):
     """(sum of squared differences, max abs difference) in FP64 on the device."""
     out = (C.c_double * 2)()

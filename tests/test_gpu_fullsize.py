@@ -84,3 +84,35 @@ def test_fullsize_step_matches_oracle(setup, precision):
             rhs = dx0[:, l * F + f].astype(np.float64).sum()
             scale = np.abs(dx0[:, l * F + f]).astype(np.float64).sum()
             assert abs(lhs - rhs) <= 1e-4 * scale, (l, f, lhs, rhs)
+
+
+@pytest.mark.parametrize("precision", [1, 0], ids=["fp16", "fp32"])
+def test_fullsize_render_inr_sampled_pixels(setup, precision):
+    # the benchmark frame (1024 x 1024 rays x 512 samples through the 256^3
+    # model, ghost 0) rendered straight from the network; sampled pixels
+    # against the oracle's march of the same rays, with the tolerance derived
+    # from the value errors at those rays' samples (see test_gpu_render_inr)
+    import test_gpu_render_inr as R
+
+    orc, dv, c, oc, vol, theta = setup
+    m = dv.Model((0, 0, 0), (256, 256, 256), 0,
+                 dv.EncodingConfig(c["L"], c["F"], c["log2T"], c["base"], c["growth"]),
+                 dv.MLPConfig(c["width"], c["hidden"]), seed=0)
+    m.set_weights(theta)
+    m.set_precision(precision)
+    w = h = 1024
+    spr = 512
+    img = dv.render_inr([m], dv.make_tf(**R.TF), w, h, spr).cpu().numpy().reshape(-1, 4)
+    rng = np.random.default_rng(3)
+    pix = rng.choice(w * h, size=48 if precision == 1 else 24, replace=False)
+    mixed = precision == 1
+    want = orc.render_inr(oc, [theta.astype(np.float64)], [(0, 0, 0)], [(256, 256, 256)], 0, 0.0,
+                          1.0, R._tf_list(), w, h, spr, pixels=pix, mixed=mixed)
+    P3, owner = R._samples([((0, 0, 0), (256, 256, 256))], w, h, spr, pix)
+    dvmax = R._value_error(dv, orc, oc, [m], [theta], [((0, 0, 0), (256, 256, 256))], 0, P3, owner,
+                           mixed)
+    assert dvmax <= (2e-3 if mixed else 2e-5), dvmax
+    bound = R.TF["alpha_max"] * spr * dvmax / (R.TF["v_hi"] - R.TF["v_lo"]) + 1e-5
+    np.testing.assert_allclose(img[pix, 3], want[:, 3], atol=bound, rtol=0)
+    np.testing.assert_allclose(img[pix, :3], want[:, :3], atol=3 * bound, rtol=0)
+    assert np.isfinite(img).all() and img[:, 3].max() <= 1.0 + 1e-6

@@ -647,3 +647,76 @@ def test_train_budget_is_train_stopped_at_the_rule(orc):
     th_r, m1_r, m2_r, st_r = fresh()
     orc.train(cfg, tc, st_r, th_r, m1_r, m2_r, vol, vmin, vmax, want)
     np.testing.assert_allclose(th_s, th_r, rtol=1e-9, atol=1e-15)
+
+
+# ------------------------------------------------- direct INR ray-marching ----
+def _zero_net(cfg):
+    return np.zeros(cfg.n_params)
+
+
+def test_render_inr_constant_network_closed_form(orc):
+    # an all-zero network outputs 0, so every sample decodes to vmin: alpha and
+    # colour are the same along every ray, A = 1 - (1 - a)^spr, C = rgb A
+    cfg = orc.Config(2, 2, 10, 4, 1.5, 16, 1)
+    tf = [0.2, 0.4, 0.6, 1.0, 0.8, 0.0, 0.05, 0.0, 1.0]
+    img = orc.render_inr(cfg, [_zero_net(cfg)], [(2, 3, 1)], [(8, 9, 7)], 1, 0.5, 1.5, tf, 5, 4, 64)
+    a = 0.05 * 0.5
+    A = 1 - (1 - a) ** 64
+    np.testing.assert_allclose(img[..., 3], A, rtol=1e-12)
+    np.testing.assert_allclose(img[..., :3], np.broadcast_to(np.array([0.6, 0.6, 0.3]) * A,
+                                                             img[..., :3].shape), rtol=1e-12)
+    # a listed subset of pixels gives the same rows
+    sub = orc.render_inr(cfg, [_zero_net(cfg)], [(2, 3, 1)], [(8, 9, 7)], 1, 0.5, 1.5, tf, 5, 4, 64,
+                         pixels=[3, 17, 0])
+    np.testing.assert_array_equal(sub, img.reshape(-1, 4)[[3, 17, 0]])
+
+
+def test_render_inr_front_to_back_two_blocks(orc):
+    # stacked blocks [0,4)^2 x [0,4) (front) and [0,4)^2 x [4,8) (back) with
+    # constant values 1 and 0.5; spr = 8 puts samples at z = 0..7, four in
+    # each. Input order must not matter (depth order is by position).
+    cfg = orc.Config(2, 2, 10, 4, 1.5, 16, 1)
+    tf = [1.0, 0.0, 0.0, 0.0, 1.0, 0.0, 0.5, 0.0, 1.0]
+    z = _zero_net(cfg)
+    args = ([(0, 0, 4), (0, 0, 0)], [(4, 4, 8), (4, 4, 4)], 1, [0.5, 1.0], [2.0, 2.0], tf, 2, 2, 8)
+    img = orc.render_inr(cfg, [z, z], *args)
+    a1, a2 = 0.5 * 1.0, 0.5 * 0.5
+    rgb1, rgb2 = np.array([0.0, 1.0, 0.0]), np.array([0.5, 0.5, 0.0])
+    A1 = 1 - (1 - a1) ** 4
+    A = 1 - (1 - a1) ** 4 * (1 - a2) ** 4
+    C = rgb1 * A1 + (1 - a1) ** 4 * rgb2 * (1 - (1 - a2) ** 4)
+    np.testing.assert_allclose(img[..., 3], A, rtol=1e-12)
+    np.testing.assert_allclose(img[..., :3], np.broadcast_to(C, img[..., :3].shape), rtol=1e-12)
+    swapped = orc.render_inr(cfg, [z, z], [(0, 0, 0), (0, 0, 4)], [(4, 4, 4), (4, 4, 8)], 1,
+                             [1.0, 0.5], [2.0, 2.0], tf, 2, 2, 8)
+    np.testing.assert_allclose(swapped, img, rtol=1e-15)
+
+
+def test_render_inr_equals_grid_march_for_a_network_affine_in_x(orc):
+    # y = 0.2 + 0.5 u_x (one dense level with affine tables, one hidden unit
+    # passing feature 0 through): the network is affine along x and constant
+    # in y and z, so marching it equals marching its decoded grid wherever
+    # the grid march interpolates (ray centres between the first and the
+    # last voxel centre in x). Checks the position -> unit-domain mapping
+    # (origin lo - ghost, stored extent), samples and compositing at once.
+    cfg = orc.Config(1, 2, 12, 6, 1.0, 16, 1)
+    th = _affine_tables(orc, cfg, [(0.2, 0.5, 0.0, 0.0), (0.0, 0.0, 0.0, 0.0)])
+    w0 = np.zeros((16, 2))
+    w0[0, 0] = 1.0
+    th[cfg.w_off[0]: cfg.w_off[0] + 32] = w0.ravel()
+    th[cfg.w_off[1]] = 1.0
+    lo, hi, ghost = (3, 1, 2), (13, 7, 10), 2
+    dims = [h - l + 2 * ghost for l, h in zip(lo, hi)]
+    vmin, vmax = -1.0, 3.0
+    grid = orc.decode_grid(cfg, th, dims, ghost, vmin, vmax)
+    tf = [0.1, 0.2, 0.6, 1.0, 0.9, 0.2, 0.08, -1.0, 3.0]
+    w, h, spr = 40, 6, 50
+    inr = orc.render_inr(cfg, [th], [lo], [hi], ghost, vmin, vmax, tf, w, h, spr)
+    ref = orc.render([grid], [lo], [hi], tf, w, h, spr)
+    X = lo[0] - 0.5 + (np.arange(w) + 0.5) * (hi[0] - lo[0]) / w
+    inside = (X >= lo[0]) & (X <= hi[0] - 1)
+    assert inside.sum() >= 30 and (~inside).sum() >= 4
+    np.testing.assert_allclose(inr[:, inside], ref[:, inside], atol=1e-7, rtol=0)
+    # outside that span the grid march clamps to the edge voxel while the
+    # network keeps its slope: the images differ there
+    assert np.abs(inr[:, ~inside] - ref[:, ~inside]).max() > 1e-4
