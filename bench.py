@@ -49,11 +49,12 @@ WORKLOADS = {
                           "32-64-64-64-1), 2^14 samples/model/step, lambda 0.15",
                      shape=(512, 1024, 1024), seed=1004, L=16, F=2, log2T=17, base=16, growth=1.38,
                      width=64, hidden=3, batch=1 << 14, steps_full=2000, lam=0.15, lr=1e-2),
-    "insitu512": dict(desc="16 advected 512^3 spectral steps, warm start, 500 iterations each, "
-                           "decode 512^3, ray-march 1024x1024x512 (L=16 F=2 T=2^19, MLP 32-64-64-64-1, "
-                           "batch 2^18, lambda 0.15)",
+    "insitu512": dict(desc="16 advected 512^3 spectral steps through a window of 8 (warm start, "
+                           "500 iterations each, older steps frozen to FP16), decode 512^3, ray-march "
+                           "1024x1024x512 (L=16 F=2 T=2^19, MLP 32-64-64-64-1, batch 2^18, lambda 0.15)",
                       shape=(512, 512, 512), seed=1005, L=16, F=2, log2T=19, base=16, growth=1.38,
-                      width=64, hidden=3, batch=1 << 18, steps_full=500, lam=0.15, lr=1e-2, t_steps=16),
+                      width=64, hidden=3, batch=1 << 18, steps_full=500, lam=0.15, lr=1e-2, t_steps=16,
+                      window=8),
     "blobs64": dict(desc="64^3 Gaussian blobs, L=8 F=2 T=2^15 N0=4 b=1.5, MLP 16-32-32-1, batch 4096",
                     shape=(64, 64, 64), seed=1001, L=8, F=2, log2T=15, base=4, growth=1.5,
                     width=32, hidden=2, batch=4096, steps_full=200, lam=0.0, lr=1e-2),
@@ -517,19 +518,21 @@ def run_insitu(args, rank, world, local_rank):
     warm.close()
     grid = torch.empty((n3, n3, n3), device=dev)
     img = torch.empty((1024, 1024, 4), device=dev)
-    prev = None
+    # the series goes through a temporal window (Sec. 4.2): each push warm-
+    # starts the new step from the newest one, trains it and freezes the
+    # previous one; the window keeps the last w["window"] steps
+    win = dv.Window([((0, 0, 0), (n3, n3, n3))], w["window"], enc, mlp, ghost=0, seed=100)
     per = []
     l0 = lib.dvnr_launch_count()
     t_train = t_dec = t_ren = 0.0
     for t in range(w["t_steps"]):
         field = volumes.advected_torch(w["shape"], w["seed"] + rank, float(t), device=dev)
-        m = dv.Model((0, 0, 0), (n3, n3, n3), 0, enc, mlp, seed=100)
-        if prev is not None:
-            m.copy_weights_from(prev)
+        torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
-        dv.train([m], [field], cfg(w["steps_full"]), sync=False)
+        win.push([field], cfg(w["steps_full"]), sync=False)
         ev[1].record(stream)
+        m = win.model(t, 0)
         m.decode_grid(grid)
         ev[2].record(stream)
         dv.render([m], tf, 1024, 1024, 512, out=img)
@@ -540,13 +543,27 @@ def run_insitu(args, rank, world, local_rank):
         t_dec += de
         t_ren += re_
         sse, _ = dv.error_stats(grid, field)
-        per.append({"t": t, "train_ms": tr, "decode_ms": de, "render_ms": re_,
+        mb, db = win.bytes()
+        per.append({"t": t, "push_ms": tr, "decode_ms": de, "render_ms": re_,
                     "psnr": 10 * math.log10(1.0 / (sse / grid.numel())),
-                    "last_loss": m.state()["last_loss"]})
-        if prev is not None:
-            prev.close()
-        prev = m
+                    "last_loss": m.state()["last_loss"], "window_device_bytes": db})
         del field
+    # the whole window visualised at the last step, straight from the cached
+    # networks (frozen FP16 models, no decoded grids)
+    first, last = win.range()
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for s_ in range(first, last + 1):
+        dv.render_inr([win.model(s_, 0)], tf, 1024, 1024, 512, out=img)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    mb, db = win.bytes()
+    window = {"capacity": w["window"], "steps_cached": last - first + 1,
+              "model_bytes_fp16": mb, "device_bytes": db,
+              "raw_grid_bytes_same_steps": (last - first + 1) * n3 ** 3 * 4,
+              "render_inr_ms_per_cached_step": r0.elapsed_time(r1) / (last - first + 1)}
+    win.close()
     launches = lib.dvnr_launch_count() - l0
     clk = clocks.stop()
     t_train = shard.max_over_ranks(t_train)
@@ -566,6 +583,7 @@ def run_insitu(args, rank, world, local_rank):
                    "ms_per_step": t_dec / T},
         "render": {"value": T * 1024 * 1024 * 512 / (t_ren / 1e3), "unit": "ray samples/s",
                    "ms_per_step_incl_decode": t_ren / T},
+        "window": window,
         "per_step": per,
     }
     return res

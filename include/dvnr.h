@@ -98,8 +98,10 @@ typedef struct {
  *   precision      DVNR_FP32: plain FP32 SIMT path, one model at a time
  *                  DVNR_FP16: FP16 tables and MLP operands on tcgen05
  *                  tensor cores, FP32 accumulation, FP32 master weights and
- *                  Adam, dynamic loss scaling; all models of the call in one
- *                  grouped launch per step
+ *                  Adam, dynamic loss scaling; all models of the call that
+ *                  share an encoding and MLP configuration in one grouped
+ *                  launch per step (models with adaptive table sizes form
+ *                  one group per configuration)
  *   loss           DVNR_LOSS_L1 (paper) or DVNR_LOSS_L2
  *   growth_interval  FP16 path: finite steps before the loss scale doubles
  *   steps          N_train: fixed iteration count of this call (>= 0),
@@ -147,7 +149,7 @@ typedef struct {
                            /*   (-1 before the first finite step)               */
   int64_t budget_end;      /* iteration at which the last call's budget ends    */
   int32_t stopped;         /* 1 when the last call stopped on stop_loss         */
-  int32_t pad;
+  int32_t frozen;          /* 1 after dvnr_freeze                               */
 } dvnr_state_info;
 
 /* Transfer function for dvnr_render: rgb = c0 + (c1 - c0) v and
@@ -184,8 +186,35 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc,
                         const dvnr_mlp_cfg* mlp, uint64_t seed,
                         dvnr_model* out);
 
+/* Adaptive encoding of a partition (Sec. 3.2: the hash table size and the
+ * base resolution follow the partition's share of the global voxel count,
+ * keeping the total model size of a decomposition near T_ref):
+ *   T   = max(2^log2_T_min, T_ref n_vox / n_vox_global rounded up to a power
+ *         of two), T_ref = 2^log2_T_ref
+ *   R_0 = floor(R_ref (T / T_ref)^(1/3)), at least 1
+ * (the paper prints T = max(T_min, T_ref ceil(N_vox / N_vox^global)), whose
+ * ceiling is 1 for every partition; the ceiling is read as applying to the
+ * product). Sets enc->log2_T and enc->base_res and leaves the other fields.
+ * Host arithmetic only (exact for integer R_ref). Errors: DVNR_E_INVALID
+ * unless 1 <= n_vox <= n_vox_global, 1 <= log2_T_min <= log2_T_ref <= 31,
+ * R_ref >= 1 and finite.                                                    */
+dvnr_status dvnr_adaptive_encoding(int64_t n_vox, int64_t n_vox_global, int32_t log2_T_ref,
+                                   int32_t log2_T_min, double R_ref, dvnr_enc_cfg* enc);
+
 /* Free a model (NULL is ignored). Synchronises the model's device.         */
 void dvnr_destroy(dvnr_model m);
+
+/* Freeze a trained model for storage (Sec. 4.2 keeps trained models for
+ * later access; Sec. 3.4 stores them as 16-bit floats): keep only its FP16
+ * parameters and value range on the device (2 bytes per parameter plus
+ * 256-byte-aligned state) and free the FP32 weights, the Adam moments, the
+ * gradients and every workspace. A frozen model decodes, renders and
+ * exports in FP16 and can warm-start another model (dvnr_copy_weights
+ * widens its FP16 parameters); training it, setting or importing its
+ * weights or switching it to FP32 returns DVNR_E_STATE. dvnr_get_weights
+ * returns the widened FP16 parameters. Synchronises `stream`; freezing a
+ * frozen model does nothing. Needs a configuration the FP16 path supports. */
+dvnr_status dvnr_freeze(dvnr_model m, void* stream);
 
 /* Parameter counts: tables (n_enc) and MLP weights (n_mlp).                */
 dvnr_status dvnr_param_count(dvnr_model m, int64_t* n_enc, int64_t* n_mlp);
@@ -278,6 +307,38 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf,
                         int32_t w, int32_t h, int32_t spr, float* rgba_dev,
                         void* stream);
 
+/* Temporal sliding window of models (Sec. 4.2: the most recent time steps
+ * stay available as trained models; when the window is full the oldest
+ * step is dropped). A step holds one model per partition (n_parts boxes,
+ * each with its own encoding, e.g. from dvnr_adaptive_encoding; one MLP).
+ *  - push: creates the step's models, warm-starts them from the newest step
+ *    (Sec. 3.5 weight caching: parameters and value range copied, Adam
+ *    reset; the first step starts from `seed` + part), trains them on the
+ *    n_parts volumes with dvnr_train(cfg), then drops the oldest step if
+ *    the window held `capacity` steps and freezes the previous newest step
+ *    (dvnr_freeze): only the newest step keeps trainable FP32 state.
+ *    *t_out = the step's index (0, 1, ...); final_loss_host as dvnr_train.
+ *    On an error the new step is discarded and the cached steps stay
+ *    (a model whose freezing failed stays trainable).
+ *  - range: indices of the oldest and newest cached steps (t_last = -1 when
+ *    empty).
+ *  - model: the model of step t and partition `part`, owned by the window:
+ *    valid until step t leaves it (or the next push, for the newest step,
+ *    which freezes it). DVNR_E_INVALID if t is not cached.
+ *  - bytes: FP16 size of the cached models (2 bytes per parameter) and the
+ *    device bytes they hold.
+ * All calls on one window must come from one thread at a time.             */
+typedef struct dvnr_window_s* dvnr_window;
+dvnr_status dvnr_window_create(const dvnr_box* boxes, int32_t n_parts, const dvnr_enc_cfg* encs,
+                               const dvnr_mlp_cfg* mlp, int32_t capacity, uint64_t seed,
+                               dvnr_window* out);
+void dvnr_window_destroy(dvnr_window w);
+dvnr_status dvnr_window_push(dvnr_window w, const float* const* vol_dev, const dvnr_train_cfg* cfg,
+                             void* stream, float* final_loss_host, int64_t* t_out);
+dvnr_status dvnr_window_range(dvnr_window w, int64_t* t_first, int64_t* t_last);
+dvnr_status dvnr_window_model(dvnr_window w, int64_t t, int32_t part, dvnr_model* out);
+dvnr_status dvnr_window_bytes(dvnr_window w, int64_t* model_bytes, int64_t* device_bytes);
+
 /* Direct volume rendering from the networks (Sec. 4.3: the renderer infers
  * the models at the ray samples instead of decoding them to grids, keeping
  * the memory footprint of the compressed form). Camera, samples, transfer
@@ -285,8 +346,9 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf,
  * block's network evaluated at the sample position (mapped into the block's
  * unit domain and clamped to it, as dvnr_decode_points), de-normalised. The
  * boxes must not overlap. All models must use one precision (the training
- * precision, or dvnr_set_precision); FP16 models must also share encoding
- * and MLP configuration. Work memory: 16 bytes per (pixel, block) pair whose
+ * precision, or dvnr_set_precision); FP16 models of different encoding or
+ * MLP configuration are marched by one launch per configuration. Work
+ * memory: 16 bytes per (pixel, block) pair whose
  * ray crosses the block (FP32 models: plus 16 bytes per sample of a chunk
  * of at most 2^24 samples), allocated stream-ordered and released before
  * return. Synchronises the stream. Errors: DVNR_E_INVALID

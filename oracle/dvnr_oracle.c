@@ -660,6 +660,35 @@ int64_t orc_max_iterations(int64_t n_vox, int64_t batch, int64_t steps,
   return n > min_steps ? n : min_steps;
 }
 
+/* Sec. 3.2 scales the hash table with the partition's share of the voxels,
+ * printed as T = max(T_min, T_ref ceil(N_vox / N_vox^global)); the ceiling
+ * of a share <= 1 is 1, so read literally T would never change. Reading: the
+ * ceiling applies to the product, rounded up to the power of two that a hash
+ * table size must be. Found by doubling from 1 in exact integer arithmetic
+ * (2^k N_vox^global >= T_ref N_vox). R_0 = floor(R_ref cbrt(T / T_ref)),
+ * taken from the FP64 cube root and corrected to the exact floor when R_ref
+ * is an integer (R^3 T_ref <= R_ref^3 T).                                     */
+void orc_adaptive_encoding(int64_t n_vox, int64_t n_vox_global, int32_t log2_T_ref,
+                           int32_t log2_T_min, double R_ref, int32_t* log2_T,
+                           int32_t* base_res) {
+  /* smallest k with 2^k n_global >= 2^log2_T_ref n_vox, in long double to
+   * keep the products exact up to 2^63 */
+  int32_t k = 0;
+  const long double need = ldexpl((long double)n_vox, log2_T_ref);
+  while (ldexpl((long double)n_vox_global, k) < need) ++k;
+  if (k < log2_T_min) k = log2_T_min;
+  *log2_T = k;
+  const double ratio = ldexp(1.0, k - log2_T_ref);
+  double r = floor(R_ref * cbrt(ratio));
+  if (R_ref == floor(R_ref)) {
+    /* exact floor for integer R_ref: largest R with R^3 <= R_ref^3 ratio */
+    const long double lim = (long double)R_ref * R_ref * R_ref * (long double)ratio;
+    while (r > 0 && (long double)r * r * r > lim) r -= 1.0;
+    while ((long double)(r + 1) * (r + 1) * (r + 1) <= lim) r += 1.0;
+  }
+  *base_res = r < 1.0 ? 1 : (int32_t)r;
+}
+
 int64_t orc_stop_step(const double* losses, const int32_t* finite, int64_t n,
                       double decay, double stop_loss, double* ema_out) {
   double m = -1.0;

@@ -119,6 +119,14 @@ double orc_train(const orc_cfg* c, const orc_train_cfg* tc, orc_state* st,
 int64_t orc_max_iterations(int64_t n_vox, int64_t batch, int64_t steps,
                            int64_t epochs, int64_t min_steps);
 
+/* Adaptive table size and base resolution of a partition (Sec. 3.2):
+ * T = max(T_min, T_ref N_vox / N_vox^global rounded up to a power of two)
+ * and R_0 = floor(R_ref (T / T_ref)^(1/3)), at least 1. T_ref = 2^log2_T_ref,
+ * T_min = 2^log2_T_min. Writes log2 T and R_0.                              */
+void orc_adaptive_encoding(int64_t n_vox, int64_t n_vox_global, int32_t log2_T_ref,
+                           int32_t log2_T_min, double R_ref, int32_t* log2_T,
+                           int32_t* base_res);
+
 /* Early stop (Sec. 3.2) over a recorded loss sequence: the moving average
  * m_1 = L_1, m_t = d m_{t-1} + (1 - d) L_t over the finite steps (finite[t]
  * != 0; a step whose gradient was non-finite leaves m unchanged), stopping

@@ -110,6 +110,8 @@ def _lib_handle():
             lib.orc_train.restype = C.c_double
             lib.orc_max_iterations.argtypes = [C.c_int64] * 5
             lib.orc_max_iterations.restype = C.c_int64
+            lib.orc_adaptive_encoding.argtypes = [C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                                  C.c_double, _P, _P]
             lib.orc_stop_step.argtypes = [_P, _P, C.c_int64, C.c_double, C.c_double, _P]
             lib.orc_stop_step.restype = C.c_int64
             lib.orc_train_budget.argtypes = [C.POINTER(_Cfg), C.POINTER(_TrainCfg),
@@ -305,6 +307,14 @@ def max_iterations(n_vox, batch, steps=0, epochs=0, min_steps=0):
     """N_train^max of one call (Sec. 3.2)."""
     return int(_lib_handle().orc_max_iterations(int(n_vox), int(batch), int(steps), int(epochs),
                                                 int(min_steps)))
+
+
+def adaptive_encoding(n_vox, n_vox_global, log2_T_ref, log2_T_min, R_ref):
+    """(log2 T, R_0) of a partition (Sec. 3.2 reading)."""
+    a, b = C.c_int32(), C.c_int32()
+    _lib_handle().orc_adaptive_encoding(int(n_vox), int(n_vox_global), int(log2_T_ref),
+                                        int(log2_T_min), float(R_ref), C.byref(a), C.byref(b))
+    return a.value, b.value
 
 
 def stop_step(losses, decay, stop_loss, finite=None):

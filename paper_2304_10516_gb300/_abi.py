@@ -29,6 +29,8 @@ EXPORTS = [
     "dvnr_render", "dvnr_error_stats", "dvnr_corner_indices", "dvnr_profile_enable",
     "dvnr_profile_read", "dvnr_launch_count", "dvnr_selftest_umma",
     "dvnr_error_stats_noalloc", "dvnr_export_fp16", "dvnr_import_fp16", "dvnr_render_inr",
+    "dvnr_adaptive_encoding", "dvnr_freeze", "dvnr_window_create", "dvnr_window_destroy",
+    "dvnr_window_push", "dvnr_window_range", "dvnr_window_model", "dvnr_window_bytes",
 ]
 
 
@@ -66,7 +68,7 @@ class dvnr_state_info(C.Structure):
                 ("skipped", C.c_int64), ("n_enc", C.c_int64), ("n_mlp", C.c_int64),
                 ("precision", C.c_int32), ("nonfinite_input", C.c_int32),
                 ("loss_ema", C.c_double), ("budget_end", C.c_int64), ("stopped", C.c_int32),
-                ("pad", C.c_int32)]
+                ("frozen", C.c_int32)]
 
 
 class dvnr_tf(C.Structure):
@@ -99,6 +101,15 @@ _SIGS = {
     "dvnr_decode_grid": ([_P, _P, _P], C.c_int),
     "dvnr_render": ([_P, C.c_int32, C.POINTER(dvnr_tf), C.c_int32, C.c_int32, C.c_int32, _P, _P],
                     C.c_int),
+    "dvnr_freeze": ([_P, _P], C.c_int),
+    "dvnr_window_create": ([_P, C.c_int32, _P, _P, C.c_int32, C.c_uint64, _P], C.c_int),
+    "dvnr_window_destroy": ([_P], None),
+    "dvnr_window_push": ([_P, _P, _P, _P, _P, _P], C.c_int),
+    "dvnr_window_range": ([_P, _P, _P], C.c_int),
+    "dvnr_window_model": ([_P, C.c_int64, C.c_int32, _P], C.c_int),
+    "dvnr_window_bytes": ([_P, _P, _P], C.c_int),
+    "dvnr_adaptive_encoding": ([C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_double,
+                                C.POINTER(dvnr_enc_cfg)], C.c_int),
     "dvnr_render_inr": ([_P, C.c_int32, C.POINTER(dvnr_tf), C.c_int32, C.c_int32, C.c_int32, _P,
                          _P], C.c_int),
     "dvnr_error_stats": ([_P, _P, C.c_int64, _P, _P], C.c_int),

@@ -29,6 +29,14 @@ dvnr_status cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? DVNR_E_OOM : DVNR_E_CUDA;
 }
 
+// Same encoding and MLP configuration: one FP16 grouped launch can hold them.
+bool same_arch(const dvnr_model a, const dvnr_model b) {
+  return a->enc.n_levels == b->enc.n_levels && a->enc.n_features == b->enc.n_features &&
+         a->enc.log2_T == b->enc.log2_T && a->enc.base_res == b->enc.base_res &&
+         a->enc.growth == b->enc.growth && a->mlp.width == b->mlp.width &&
+         a->mlp.n_hidden == b->mlp.n_hidden;
+}
+
 namespace {
 
 dvnr_status fail(dvnr_status s, const char* fmt, ...) {
@@ -88,12 +96,6 @@ dvnr_status check_enc_mlp(const dvnr_enc_cfg* enc, const dvnr_mlp_cfg* mlp) {
   return DVNR_OK;
 }
 
-bool same_arch(const dvnr_model a, const dvnr_model b) {
-  return a->enc.n_levels == b->enc.n_levels && a->enc.n_features == b->enc.n_features &&
-         a->enc.log2_T == b->enc.log2_T && a->enc.base_res == b->enc.base_res &&
-         a->enc.growth == b->enc.growth && a->mlp.width == b->mlp.width &&
-         a->mlp.n_hidden == b->mlp.n_hidden;
-}
 
 dvnr_status check_train_cfg(const dvnr_train_cfg* c) {
   if (!c) return fail(DVNR_E_INVALID, "NULL train configuration");
@@ -282,7 +284,8 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
   const size_t P = (size_t)m->n_store;
   const size_t b32 = align256(P * 4), b16 = align256(P * 2), bst = align256(sizeof(ModelState)),
                bq = align256((kQTab + 1) * sizeof(int32_t)), bap = align256(sizeof(AdamModelPtrs));
-  ce = cudaMalloc(&m->block, 4 * b32 + b16 + bst + bq + bap);
+  m->block_bytes = 4 * b32 + b16 + bst + bq + bap;
+  ce = cudaMalloc(&m->block, m->block_bytes);
   if (ce != cudaSuccess) {
     delete m;
     return cuda_status(ce, "cudaMalloc(model)");
@@ -333,6 +336,46 @@ void dvnr_destroy(dvnr_model m) {
   delete m;
 }
 
+dvnr_status dvnr_freeze(dvnr_model m, void* stream) {
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (m->frozen) return DVNR_OK;
+  if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  DVNR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if ((rc = launch_refresh_half(m, (cudaStream_t)stream)) != DVNR_OK) return rc;
+  const size_t b16 = align256((size_t)m->n_store * 2), bst = align256(sizeof(ModelState));
+  void* blk = nullptr;
+  DVNR_CUDA(cudaMalloc(&blk, b16 + bst));
+  char* p = static_cast<char*>(blk);
+  cudaError_t e = cudaMemcpyAsync(p, m->theta16, (size_t)m->n_store * 2, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p + b16, m->st, sizeof(ModelState), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaFree(blk);
+    return cuda_status(e, "dvnr_freeze");
+  }
+  mp_release(m);
+  if (m->ws.base) cudaFree(m->ws.base);
+  m->ws = Fp32Workspace{};
+  if (m->grid_ws) cudaFree(m->grid_ws);
+  m->grid_ws = nullptr;
+  m->grid_ws_elems = 0;
+  cudaFree(m->block);
+  m->block = blk;
+  m->block_bytes = b16 + bst;
+  m->theta = m->m1 = m->m2 = m->grad = nullptr;
+  m->qtab = nullptr;
+  m->qtab_sigma = -1.f;
+  m->theta16 = reinterpret_cast<__half*>(p);
+  m->st = reinterpret_cast<ModelState*>(p + b16);
+  m->precision = DVNR_FP16;
+  m->frozen = true;
+  return DVNR_OK;
+}
+
 dvnr_status dvnr_param_count(dvnr_model m, int64_t* n_enc, int64_t* n_mlp) {
   if (!m) return fail(DVNR_E_INVALID, "model is NULL");
   if (n_enc) *n_enc = m->n_enc;
@@ -357,13 +400,42 @@ dvnr_status copy_blocks(dvnr_model m, float* host, const float* host_src, bool t
 }  // namespace
 }  // namespace dvnr
 
+dvnr_status dvnr_adaptive_encoding(int64_t n_vox, int64_t n_vox_global, int32_t log2_T_ref,
+                                   int32_t log2_T_min, double R_ref, dvnr_enc_cfg* enc) {
+  if (!enc) return fail(DVNR_E_INVALID, "NULL encoding configuration");
+  if (n_vox < 1 || n_vox > n_vox_global) return fail(DVNR_E_INVALID, "need 1 <= n_vox <= n_vox_global");
+  if (log2_T_min < 1 || log2_T_min > log2_T_ref || log2_T_ref > 31)
+    return fail(DVNR_E_INVALID, "need 1 <= log2_T_min <= log2_T_ref <= 31");
+  if (!(R_ref >= 1.0) || !std::isfinite(R_ref)) return fail(DVNR_E_INVALID, "R_ref must be finite and >= 1");
+  // T = 2^k with k the smallest exponent such that 2^k n_global >= T_ref n_vox
+  const unsigned __int128 want = (unsigned __int128)(uint64_t)n_vox << log2_T_ref;
+  int k = 0;
+  while (((unsigned __int128)(uint64_t)n_vox_global << k) < want) ++k;
+  k = std::max(k, (int)log2_T_min);
+  // R_0: the largest R with R^3 T_ref <= R_ref^3 T (exact when R_ref is an
+  // integer), else from the cube root
+  int64_t r;
+  const int e = k - log2_T_ref;  // <= 0 since n_vox <= n_vox_global
+  if (R_ref == std::floor(R_ref) && R_ref < 1e6) {
+    const unsigned __int128 rr = (unsigned __int128)(uint64_t)R_ref;
+    const unsigned __int128 rhs = rr * rr * rr;  // R_ref^3, compared as R^3 2^-e <= R_ref^3
+    r = (int64_t)R_ref;
+    while (r > 1 && (((unsigned __int128)r * r * r) << (-e)) > rhs) --r;
+  } else {
+    r = (int64_t)std::floor(R_ref * std::cbrt(std::ldexp(1.0, e)));
+  }
+  enc->log2_T = k;
+  enc->base_res = (int32_t)std::max<int64_t>(1, r);
+  return DVNR_OK;
+}
+
 dvnr_status dvnr_export_fp16(dvnr_model m, uint16_t* host, int64_t n) {
   if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
   if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
   DVNR_CUDA(cudaDeviceSynchronize());
-  if ((rc = launch_refresh_half(m, 0)) != DVNR_OK) return rc;  // the copy follows the master weights
+  if (!m->frozen && (rc = launch_refresh_half(m, 0)) != DVNR_OK) return rc;  // the copy follows the master weights
   DVNR_CUDA(cudaDeviceSynchronize());
   for (int b = 0; b <= m->lmap.L; ++b) {
     const int64_t e0 = m->lmap.ext_off[b], len = m->lmap.ext_off[b + 1] - e0;
@@ -375,6 +447,7 @@ dvnr_status dvnr_export_fp16(dvnr_model m, uint16_t* host, int64_t n) {
 
 dvnr_status dvnr_import_fp16(dvnr_model m, const uint16_t* host, int64_t n) {
   if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
+  if (m->frozen) return fail(DVNR_E_STATE, "the model is frozen");
   if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
@@ -400,11 +473,18 @@ dvnr_status dvnr_get_weights(dvnr_model m, float* host, int64_t n) {
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
   DVNR_CUDA(cudaDeviceSynchronize());
+  if (m->frozen) {  // the FP16 parameters, widened
+    std::vector<uint16_t> h16((size_t)n);
+    if ((rc = dvnr_export_fp16(m, h16.data(), n)) != DVNR_OK) return rc;
+    for (int64_t i = 0; i < n; ++i) host[i] = __half2float(__ushort_as_half(h16[(size_t)i]));
+    return DVNR_OK;
+  }
   return copy_blocks(m, host, nullptr, true);
 }
 
 dvnr_status dvnr_set_weights(dvnr_model m, const float* host, int64_t n) {
   if (!m || !host) return fail(DVNR_E_INVALID, "NULL argument");
+  if (m->frozen) return fail(DVNR_E_STATE, "the model is frozen");
   if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
@@ -424,13 +504,18 @@ dvnr_status dvnr_copy_weights(dvnr_model dst, dvnr_model src, void* stream) {
   if (!dst || !src) return fail(DVNR_E_INVALID, "NULL model");
   if (!same_arch(dst, src)) return fail(DVNR_E_INVALID, "models differ in encoding or MLP configuration");
   if (dst->device != src->device) return fail(DVNR_E_INVALID, "models live on different devices");
+  if (dst->frozen) return fail(DVNR_E_STATE, "the destination model is frozen");
   if (dst == src) return DVNR_OK;
   dvnr_status rc = use_device(dst);
   if (rc != DVNR_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)dst->n_store;
-  DVNR_CUDA(cudaMemcpyAsync(dst->theta, src->theta, n * 4, cudaMemcpyDeviceToDevice, s));
   DVNR_CUDA(cudaMemcpyAsync(dst->theta16, src->theta16, n * 2, cudaMemcpyDeviceToDevice, s));
+  if (src->frozen) {  // a frozen source has only its FP16 parameters: widen them
+    if ((rc = launch_widen_half(dst, s)) != DVNR_OK) return rc;
+  } else {
+    DVNR_CUDA(cudaMemcpyAsync(dst->theta, src->theta, n * 4, cudaMemcpyDeviceToDevice, s));
+  }
   DVNR_CUDA(cudaMemcpyAsync(dst->st, src->st, 2 * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   DVNR_CUDA(cudaMemsetAsync(dst->m1, 0, n * 4, s));
   DVNR_CUDA(cudaMemsetAsync(dst->m2, 0, n * 4, s));
@@ -446,6 +531,7 @@ dvnr_status dvnr_set_precision(dvnr_model m, int32_t precision, void* stream) {
   if (precision != DVNR_FP32 && precision != DVNR_FP16) return fail(DVNR_E_INVALID, "bad precision");
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
+  if (m->frozen && precision != DVNR_FP16) return fail(DVNR_E_STATE, "a frozen model decodes in FP16 only");
   if (precision == DVNR_FP16 && m->precision != DVNR_FP16) {
     if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
     if ((rc = launch_refresh_half(m, (cudaStream_t)stream)) != DVNR_OK) return rc;
@@ -475,7 +561,7 @@ dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out) {
   out->loss_ema = st.loss_ema;
   out->budget_end = st.stop_at;
   out->stopped = st.stopped ? 1 : 0;
-  out->pad = 0;
+  out->frozen = m->frozen ? 1 : 0;
   if (st.timeouts) return fail(DVNR_E_TIMEOUT, "a bounded device wait gave up (%u)", st.timeouts);
   if (st.nonfinite) return fail(DVNR_E_NONFINITE_INPUT, "the last training volume held NaN/Inf");
   return DVNR_OK;
@@ -489,18 +575,16 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
   if (rc != DVNR_OK) return rc;
   for (int i = 0; i < n; ++i) {
     if (!models[i] || !vol_dev[i]) return fail(DVNR_E_INVALID, "model or volume %d is NULL", i);
+    if (models[i]->frozen) return fail(DVNR_E_STATE, "model %d is frozen", i);
     if (models[i]->device != models[0]->device) return fail(DVNR_E_INVALID, "models on different devices");
     for (int j = 0; j < i; ++j)
       if (models[j] == models[i]) return fail(DVNR_E_INVALID, "model %d appears twice", i);
   }
   const bool mixed = cfg->precision == DVNR_FP16;
   if (mixed) {
-    for (int i = 0; i < n; ++i) {
-      if (!same_arch(models[i], models[0]))
-        return fail(DVNR_E_INVALID, "grouped FP16 training needs one configuration for all models");
+    for (int i = 0; i < n; ++i)
       if (!mp_supported(models[i]))
         return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
-    }
   }
   std::vector<int64_t> budget((size_t)n);
   int64_t max_budget = 0;
@@ -524,9 +608,37 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
   }
   const AdamHyper h = adam_hyper(cfg, mixed);
   if (mixed) {
-    const bool uniform = std::all_of(budget.begin(), budget.end(), [&](int64_t b) { return b == max_budget; });
-    if (max_budget > 0 && (rc = mp_train(models, n, vol_dev, cfg, h, max_budget, uniform, s)) != DVNR_OK)
-      return rc;
+    // one grouped launch per configuration class (models of a decomposition
+    // with adaptive table sizes differ in T and R_0); each model keeps its
+    // RNG slot, its index in this call
+    std::vector<std::vector<int>> classes;
+    for (int i = 0; i < n; ++i) {
+      bool placed = false;
+      for (auto& c : classes)
+        if (same_arch(models[c[0]], models[i])) {
+          c.push_back(i);
+          placed = true;
+          break;
+        }
+      if (!placed) classes.push_back({i});
+    }
+    for (const auto& c : classes) {
+      std::vector<dvnr_model> cm;
+      std::vector<const float*> cv;
+      std::vector<uint32_t> slots;
+      int64_t cmax = 0;
+      for (int i : c) {
+        cm.push_back(models[i]);
+        cv.push_back(vol_dev[i]);
+        slots.push_back((uint32_t)i);
+        cmax = std::max(cmax, budget[i]);
+      }
+      bool uniform = true;
+      for (int i : c) uniform &= budget[i] == cmax;
+      if (cmax > 0 && (rc = mp_train(cm.data(), (int)c.size(), cv.data(), slots.data(), cfg, h, cmax,
+                                     uniform, s)) != DVNR_OK)
+        return rc;
+    }
   } else {
     for (int i = 0; i < n; ++i) {
       dvnr_model m = models[i];
@@ -565,6 +677,7 @@ dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev, const dvnr_train
                             int64_t iteration, const dvnr_step_outputs* out, void* stream) {
   g_err[0] = 0;
   if (!m || !vol_dev) return fail(DVNR_E_INVALID, "NULL model or volume");
+  if (m->frozen) return fail(DVNR_E_STATE, "the model is frozen");
   dvnr_status rc = check_train_cfg(cfg);
   if (rc != DVNR_OK) return rc;
   if (iteration < 0) return fail(DVNR_E_INVALID, "iteration must be >= 0");
@@ -684,12 +797,8 @@ dvnr_status dvnr_render_inr(const dvnr_model* models, int32_t n, const dvnr_tf* 
     if (models[i]->device != models[0]->device) return fail(DVNR_E_INVALID, "models on different devices");
     if (models[i]->precision != models[0]->precision)
       return fail(DVNR_E_INVALID, "model %d: all models must use one precision", i);
-    if (models[0]->precision == DVNR_FP16) {
-      if (!same_arch(models[i], models[0]))
-        return fail(DVNR_E_INVALID, "FP16 rendering needs one configuration for all models");
-      if (!mp_supported(models[i]))
-        return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
-    }
+    if (models[0]->precision == DVNR_FP16 && !mp_supported(models[i]))
+      return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
   }
   dvnr_status rc = use_device(models[0]);
   if (rc != DVNR_OK) return rc;

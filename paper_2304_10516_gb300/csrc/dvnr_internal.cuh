@@ -152,6 +152,7 @@ struct dvnr_model_s {
   double glorot[dvnr::kMaxHidden + 1] = {};  // init limit of each matrix
   // parameter block: theta | m1 | m2 | grad (fp32), theta16, state, qtab
   void* block = nullptr;
+  size_t block_bytes = 0;       // device bytes of `block`
   float* theta = nullptr;
   float* m1 = nullptr;
   float* m2 = nullptr;
@@ -162,6 +163,9 @@ struct dvnr_model_s {
   float qtab_sigma = -1.f;
   int32_t precision = DVNR_FP32;
   bool scale_initialized = false;  // FP16 loss scale set for this model
+  // frozen: only the FP16 parameters and the state remain (theta, m1, m2,
+  // grad and qtab are NULL); decodes and renders in FP16, cannot train
+  bool frozen = false;
   dvnr::Fp32Workspace ws;
   void* mp = nullptr;              // FP16 path resources (mp_path.cu)
   float* grid_ws = nullptr;  // decoded grid for rendering
@@ -347,6 +351,9 @@ struct RenderBlock {
 dvnr_status launch_render(const RenderBlock* blocks_dev, int n_blocks, const float lo[3],
                           const float hi[3], const dvnr_tf& tf, int w, int h, int spr,
                           float* rgba, cudaStream_t s);
+// Same encoding and MLP configuration (api.cu).
+bool same_arch(const dvnr_model a, const dvnr_model b);
+
 // Direct INR ray-marching (render_inr.cu): same camera and transfer function
 // as launch_render, values from the models' networks at the ray samples.
 // All models share one precision; FP16 models also one architecture.

@@ -850,6 +850,7 @@ void launch_decode_wf(const MpDecodeParams& p, int grid, cudaStream_t s) {
 struct MpCache {
   std::vector<dvnr_model> models;
   std::vector<const float*> vols;
+  std::vector<uint32_t> slots;
   dvnr_train_cfg cfg{};
   int graph_steps = 0;
   MpModel* d_models = nullptr;
@@ -881,6 +882,7 @@ struct MpCache {
     cap = nullptr;
     models.clear();
     vols.clear();
+    slots.clear();
     graph_steps = 0;
   }
 };
@@ -1100,8 +1102,9 @@ void mp_release(dvnr_model m) {
   }
 }
 
-dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const dvnr_train_cfg* cfg,
-                     const AdamHyper& h, int64_t steps, bool uniform, cudaStream_t s) {
+dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const uint32_t* slots,
+                     const dvnr_train_cfg* cfg, const AdamHyper& h, int64_t steps, bool uniform,
+                     cudaStream_t s) {
   dvnr_model m0 = models[0];
   MpLayout lay;
   if (!make_layout(m0, true, lay)) {
@@ -1111,7 +1114,8 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   if (!m0->mp) m0->mp = new MpCache();
   MpCache* c = static_cast<MpCache*>(m0->mp);
   bool hit = c->d_models && (int)c->models.size() == n && same_cfg(c->cfg, *cfg);
-  for (int i = 0; hit && i < n; ++i) hit = c->models[i] == models[i] && c->vols[i] == vols[i];
+  for (int i = 0; hit && i < n; ++i)
+    hit = c->models[i] == models[i] && c->vols[i] == vols[i] && c->slots[i] == slots[i];
   if (!hit) {
     if (c->d_models) DVNR_CUDA(cudaStreamSynchronize(s));
     c->clear();
@@ -1120,7 +1124,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     for (int i = 0; i < n; ++i) {
       dvnr_model m = models[i];
       hm[i] = MpModel{m->theta16, m->grad, vols[i], (int32_t)m->dims[0], (int32_t)m->dims[1],
-                      (int32_t)m->dims[2], (uint32_t)i, m->st};
+                      (int32_t)m->dims[2], slots[i], m->st};
       ha[i] = AdamModelPtrs{m->theta, m->m1, m->m2, m->grad, m->theta16, m->st};
     }
     DVNR_CUDA(cudaMalloc(&c->d_models, sizeof(MpModel) * n));
@@ -1130,6 +1134,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     DVNR_CUDA(cudaMemcpy(c->d_adam, ha.data(), sizeof(AdamModelPtrs) * n, cudaMemcpyHostToDevice));
     c->models.assign(models, models + n);
     c->vols.assign(vols, vols + n);
+    c->slots.assign(slots, slots + n);
     c->cfg = *cfg;
   }
   MpParams p = base_params(m0, lay, cfg);

@@ -20,9 +20,11 @@ void mp_release(dvnr_model m);
 // `steps` grouped steps of the n models (schedule, fused kernel, reduction,
 // Adam per step); a model leaves the steps once model_active is false.
 // `uniform`: every model's budget equals `steps` (with no stop rule the
-// schedule kernel is then skipped).
-dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const dvnr_train_cfg* cfg,
-                     const AdamHyper& h, int64_t steps, bool uniform, cudaStream_t s);
+// schedule kernel is then skipped). All n models share one configuration;
+// model i draws its samples with RNG slot slots[i].
+dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const uint32_t* slots,
+                     const dvnr_train_cfg* cfg, const AdamHyper& h, int64_t steps, bool uniform,
+                     cudaStream_t s);
 // One forward/backward of model slot 0 at iteration `iter` and loss scale S,
 // gradients left (scaled by S) in m->grad.
 dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* cfg, uint32_t iter,

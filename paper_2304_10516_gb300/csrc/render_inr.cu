@@ -363,27 +363,64 @@ dvnr_status render_inr(const dvnr_model* models, int n, const dvnr_tf& tf, int w
     n_ray += rays;
     n_grp += (rays + kGroup - 1) / kGroup;
   }
+  // FP16: one fused launch per configuration class, each over a table of
+  // its blocks with groups renumbered from 0 (composites keep their global
+  // ray0); the depth-ordered table for the final blend follows them
+  std::vector<std::vector<int>> classes;  // indices into `blocks`
+  if (fp16) {
+    for (int j = 0; j < n; ++j) {
+      const dvnr_model m = models[order[(size_t)j]];
+      bool placed = false;
+      for (auto& c : classes)
+        if (same_arch(models[order[(size_t)c[0]]], m)) {
+          c.push_back(j);
+          placed = true;
+          break;
+        }
+      if (!placed) classes.push_back({j});
+    }
+  }
+  std::vector<InrBlock> table(blocks);
+  std::vector<int64_t> class_grps;
+  for (const auto& c : classes) {
+    int64_t g = 0;
+    for (int j : c) {
+      InrBlock bk = blocks[(size_t)j];
+      bk.grp0 = g;
+      g += ((int64_t)bk.npx * bk.npy + kGroup - 1) / kGroup;
+      table.push_back(bk);
+    }
+    class_grps.push_back(g);
+  }
   InrBlock* dblocks = nullptr;
   float4* part = nullptr;
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dblocks), blocks.size() * sizeof(InrBlock), s));
-  DVNR_CUDA(cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(InrBlock),
+  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dblocks), table.size() * sizeof(InrBlock), s));
+  DVNR_CUDA(cudaMemcpyAsync(dblocks, table.data(), table.size() * sizeof(InrBlock),
                             cudaMemcpyHostToDevice, s));
   DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&part), (size_t)std::max<int64_t>(n_ray, 1) * sizeof(float4), s));
   dvnr_status rc = DVNR_OK;
   if (n_grp > 0 && fp16) {
-    const dvnr_model m0 = models[0];
-    InrParams p{};
-    if (!make_layout(m0, false, p.lay)) {
-      set_error("FP16 path: configuration exceeds shared or tensor memory");
-      rc = DVNR_E_UNSUPPORTED;
-    } else {
+    size_t first = (size_t)n;
+    for (size_t ci = 0; ci < classes.size() && rc == DVNR_OK; ++ci) {
+      const dvnr_model m0 = models[order[(size_t)classes[ci][0]]];
+      const size_t nb = classes[ci].size();
+      InrParams p{};
+      if (class_grps[ci] == 0) {
+        first += nb;
+        continue;
+      }
+      if (!make_layout(m0, false, p.lay)) {
+        set_error("FP16 path: configuration exceeds shared or tensor memory");
+        rc = DVNR_E_UNSUPPORTED;
+        break;
+      }
       p.lv = m0->lv;
       p.D = m0->lv.in_dim;
       p.H = m0->mlp.n_hidden;
       for (int k = 0; k <= m0->mlp.n_hidden; ++k) p.w_off[k] = m0->w_off[k];
-      p.blocks = dblocks;
-      p.n_blocks = n;
-      p.n_grp = n_grp;
+      p.blocks = dblocks + first;
+      p.n_blocks = (int32_t)nb;
+      p.n_grp = class_grps[ci];
       p.fr = fr;
       p.part = part;
       const int W = m0->mlp.width, F = m0->lv.F;
@@ -393,6 +430,7 @@ dvnr_status render_inr(const dvnr_model* models, int n, const dvnr_tf& tf, int w
       }
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_status(e, "render_inr");
+      first += nb;
     }
   } else if (n_grp > 0) {
     // sample streaming in chunks of rays, at most ~2^24 samples per chunk

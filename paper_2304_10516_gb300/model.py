@@ -23,6 +23,18 @@ class EncodingConfig:
     growth: float = 1.38
 
 
+def adaptive_encoding(n_vox: int, n_vox_global: int, log2_T_ref: int = 19, log2_T_min: int = 12,
+                      R_ref: float = 16.0, base: EncodingConfig | None = None) -> EncodingConfig:
+    """The encoding of a partition with n_vox of n_vox_global voxels: table
+    size and base resolution scaled with its share (Sec. 3.2); the other
+    fields from `base`."""
+    base = base or EncodingConfig()
+    ec = A.dvnr_enc_cfg(base.n_levels, base.n_features, base.log2_T, base.base_res, float(base.growth))
+    A.call("dvnr_adaptive_encoding", int(n_vox), int(n_vox_global), int(log2_T_ref), int(log2_T_min),
+           float(R_ref), C.byref(ec))
+    return EncodingConfig(base.n_levels, base.n_features, ec.log2_T, ec.base_res, base.growth)
+
+
 @dataclass
 class MLPConfig:
     """ReLU MLP (appendix keys n_neurons, n_hidden_layers)."""
@@ -90,11 +102,31 @@ class Model:
         self.n_enc, self.n_mlp = ne.value, nm.value
         self.n_params = self.n_enc + self.n_mlp
 
+    @classmethod
+    def _borrowed(cls, handle, lo, hi, ghost, enc, mlp):
+        """A view of a model owned by the library (e.g. by a Window): closing
+        or collecting it does not free the model."""
+        m = cls.__new__(cls)
+        m.lo, m.hi, m.ghost = tuple(int(v) for v in lo), tuple(int(v) for v in hi), int(ghost)
+        m.enc, m.mlp = enc, mlp
+        m._h = handle
+        m._owned = False
+        ne, nm = C.c_int64(), C.c_int64()
+        A.call("dvnr_param_count", handle, C.byref(ne), C.byref(nm))
+        m.n_enc, m.n_mlp = ne.value, nm.value
+        m.n_params = m.n_enc + m.n_mlp
+        return m
+
     # ------------------------------------------------------------ lifecycle
     def close(self):
         if getattr(self, "_h", None):
-            A.load().dvnr_destroy(self._h)
+            if getattr(self, "_owned", True):
+                A.load().dvnr_destroy(self._h)
             self._h = None
+
+    def freeze(self, stream=None):
+        """Keep only the FP16 parameters and value range (storage form)."""
+        A.call("dvnr_freeze", self._h, _stream(stream))
 
     def __del__(self):
         try:
@@ -224,6 +256,66 @@ def render(models, tf, w, h, spr, out=None, stream=None):
     A.call("dvnr_render", C.cast(hs, C.c_void_p), n, C.byref(tf), w, h, spr, _ptr(out),
            _stream(stream))
     return out
+
+
+class Window:
+    """Temporal sliding window of trained models (Sec. 4.2): one model per
+    partition and time step, the newest step trainable, older steps frozen,
+    at most `capacity` steps."""
+
+    def __init__(self, boxes, capacity, encs=None, mlp: MLPConfig | None = None, ghost=1,
+                 seed: int = 0):
+        self.boxes = [(tuple(lo), tuple(hi)) for lo, hi in boxes]
+        n = len(self.boxes)
+        if encs is None or isinstance(encs, EncodingConfig):
+            encs = [encs or EncodingConfig()] * n
+        self.encs, self.mlp, self.ghost = list(encs), mlp or MLPConfig(), int(ghost)
+        cb = (A.dvnr_box * n)(*[A.dvnr_box((C.c_int64 * 3)(*lo), (C.c_int64 * 3)(*hi), self.ghost)
+                                for lo, hi in self.boxes])
+        ce = (A.dvnr_enc_cfg * n)(*[A.dvnr_enc_cfg(e.n_levels, e.n_features, e.log2_T, e.base_res,
+                                                   float(e.growth)) for e in self.encs])
+        mc = A.dvnr_mlp_cfg(self.mlp.width, self.mlp.n_hidden)
+        h = C.c_void_p()
+        A.call("dvnr_window_create", C.cast(cb, C.c_void_p), n, C.cast(ce, C.c_void_p),
+               C.byref(mc), int(capacity), int(seed), C.byref(h))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            A.load().dvnr_window_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, volumes, cfg: TrainConfig, stream=None, sync: bool = True):
+        n = len(self.boxes)
+        vs = (C.c_void_p * n)(*[v.data_ptr() for v in volumes])
+        c = cfg.to_c()
+        losses = (C.c_float * n)() if sync else None
+        t = C.c_int64()
+        A.call("dvnr_window_push", self._h, C.cast(vs, C.c_void_p), C.byref(c), _stream(stream),
+               C.cast(losses, C.c_void_p) if sync else None, C.byref(t))
+        return t.value, ([float(v) for v in losses] if sync else None)
+
+    def range(self):
+        a, b = C.c_int64(), C.c_int64()
+        A.call("dvnr_window_range", self._h, C.byref(a), C.byref(b))
+        return a.value, b.value
+
+    def model(self, t: int, part: int = 0) -> Model:
+        h = C.c_void_p()
+        A.call("dvnr_window_model", self._h, int(t), int(part), C.byref(h))
+        lo, hi = self.boxes[part]
+        return Model._borrowed(h, lo, hi, self.ghost, self.encs[part], self.mlp)
+
+    def bytes(self):
+        a, b = C.c_int64(), C.c_int64()
+        A.call("dvnr_window_bytes", self._h, C.byref(a), C.byref(b))
+        return a.value, b.value
 
 
 def render_inr(models, tf, w, h, spr, out=None, stream=None):

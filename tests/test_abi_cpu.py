@@ -7,6 +7,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2304_10516_gb300 import _abi as A
@@ -126,3 +127,21 @@ def test_python_package_has_no_cpu_fallback():
     src = open(os.path.join(ROOT, "paper_2304_10516_gb300", "model.py")).read()
     assert "oracle" not in src
     assert "import torch.nn" not in src
+
+
+def test_adaptive_encoding_matches_oracle(orc):
+    # host arithmetic of the library (no device work) against the oracle
+    from paper_2304_10516_gb300 import model as dv
+
+    rng = np.random.default_rng(11)
+    cases = [(512 ** 3, 512 ** 3), (256 ** 3, 512 ** 3), (96 * 130 * 150, 512 ** 3),
+             (2 ** 27 + 1, 2 ** 30), (1, 10 ** 9)]
+    cases += [(int(v), int(g)) for g, v in
+              ((g, rng.integers(1, g + 1)) for g in rng.integers(10 ** 6, 10 ** 10, 100))]
+    for n_vox, n_glob in cases:
+        for lref, lmin, rref in ((19, 12, 16.0), (17, 10, 20.0), (22, 14, 7.5)):
+            e = dv.adaptive_encoding(n_vox, n_glob, lref, lmin, rref)
+            assert (e.log2_T, e.base_res) == orc.adaptive_encoding(n_vox, n_glob, lref, lmin, rref), \
+                (n_vox, n_glob, lref, lmin, rref)
+    with pytest.raises(A.DvnrError):
+        dv.adaptive_encoding(10, 5)

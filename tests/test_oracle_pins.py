@@ -720,3 +720,37 @@ def test_render_inr_equals_grid_march_for_a_network_affine_in_x(orc):
     # outside that span the grid march clamps to the edge voxel while the
     # network keeps its slope: the images differ there
     assert np.abs(inr[:, ~inside] - ref[:, ~inside]).max() > 1e-4
+
+
+# ------------------------------------------------- adaptive T and R_0 ----
+def test_adaptive_encoding_closed_forms(orc):
+    # T_ref N_vox / N_global rounded up to a power of two, floored at T_min;
+    # R_0 = floor(R_ref cbrt(T / T_ref)), checked with exact fractions
+    Tref, Tmin, Rref = 19, 12, 16
+    cases = [
+        (512 ** 3, 512 ** 3, 19, 16),                 # one partition: T = T_ref, R_0 = R_ref
+        (256 ** 3, 512 ** 3, 16, 8),                  # an eighth: T_ref / 8, R_0 = R_ref / 2
+        (128 ** 3, 512 ** 3, 13, 4),                  # 1/64: T_ref / 64, R_0 = R_ref / 4
+        (64 ** 3, 512 ** 3, 12, 3),                   # 1/512 -> 2^10, floored at T_min = 2^12
+        (96 * 130 * 150, 512 ** 3, 13, 4),            # 2^19 / 71.7 = 7312 -> 2^13; 16 cbrt(1/64) = 4
+        (2 ** 27 + 1, 2 ** 30, 17, 10),               # just above 1/8 of 2^30 -> 2^17; 16 cbrt(1/4)
+    ]
+    for n_vox, n_glob, want_T, want_R in cases:
+        assert orc.adaptive_encoding(n_vox, n_glob, Tref, Tmin, Rref) == (want_T, want_R)
+    # the general case against exact rational arithmetic
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        n_glob = int(rng.integers(10 ** 6, 10 ** 9))
+        n_vox = int(rng.integers(1, n_glob + 1))
+        lt, r0 = orc.adaptive_encoding(n_vox, n_glob, Tref, Tmin, Rref)
+        share = Fraction(2 ** Tref * n_vox, n_glob)
+        k = 0
+        while Fraction(2 ** k) < share:
+            k += 1
+        k = max(k, Tmin)
+        assert lt == k
+        ratio = Fraction(2 ** k, 2 ** Tref)
+        R = 1
+        while Fraction((R + 1) ** 3) <= Rref ** 3 * ratio:
+            R += 1
+        assert r0 == R, (n_vox, n_glob, k, r0, R)
