@@ -38,9 +38,12 @@ namespace dvnr {
 
 namespace {
 
+#ifndef DVNR_TRAIN_STAGED
+#define DVNR_TRAIN_STAGED 1
+#endif
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
-[[maybe_unused]] constexpr int kTrainKernelRevision = 7;
+[[maybe_unused]] constexpr int kTrainKernelRevision = 8;
 
 struct MpModel {
   const __half* theta16;
@@ -304,7 +307,15 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     const uint3 mc = valid ? draw_sample(sp, (uint32_t)i, iter) : make_uint3(0u, 0u, 0u);
     VolCorners vc{};
     if (valid) vc = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc);  // in flight during the encode
-    encode_to_tile<F, DVNR_TRAIN_PAIR>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
+#if DVNR_TRAIN_STAGED
+    if constexpr (F == 2) {
+      // all gathers of the tile in flight at once, staged in the dZ tile and
+      // the hidden-activation tiles (idle until the forward pass)
+      encode_to_tile_staged(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid, s_dz, H * W / 16,
+                            s_act + (uint32_t)D * 256u, (H - 1) * W / 16);
+    } else
+#endif
+      encode_to_tile<F, DVNR_TRAIN_PAIR>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
     const float target = valid ? (vol_interp(vc) - vmin) * inv_range : 0.f;
     umma::fence_proxy_async();
     umma::fence_before_sync();
