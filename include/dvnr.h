@@ -307,6 +307,29 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf,
                         int32_t w, int32_t h, int32_t spr, float* rgba_dev,
                         void* stream);
 
+/* Rendering in a given frame, for sort-last compositing (Sec. 4.3: every
+ * rank renders its own partitions, the images are blended in depth order).
+ * As dvnr_render (from_network = 0: decoded grids) or dvnr_render_inr
+ * (from_network = 1: the networks), but the camera spans the box
+ * [frame_lo, frame_hi) (global voxel indices, hi > lo per axis) instead of
+ * the union of the models' boxes, so images of disjoint partition sets
+ * rendered apart in one frame align pixel for pixel and sample for sample;
+ * pixels whose ray misses the models are (0, 0, 0, 0).                     */
+dvnr_status dvnr_render_in_frame(const dvnr_model* models, int32_t n, const int64_t frame_lo[3],
+                                 const int64_t frame_hi[3], const dvnr_tf* tf, int32_t w,
+                                 int32_t h, int32_t spr, int32_t from_network, float* rgba_dev,
+                                 void* stream);
+
+/* Sort-last compositing (Sec. 4.3): blend n premultiplied RGBA images of one
+ * frame (w x h x 4 float32 on the device each) front to back in increasing
+ * depth_host[i] (e.g. the lo.z of the partitions each was rendered from;
+ * ties keep the input order): C += (1 - A) C_i, A += (1 - A) A_i. For
+ * partitions whose boxes are disjoint and ordered along +z this gives the
+ * image of their union (up to rounding order). out_dev may not alias an
+ * input. Synchronises the stream.                                           */
+dvnr_status dvnr_composite(const float* const* rgba_dev, const double* depth_host, int32_t n,
+                           int32_t w, int32_t h, float* out_dev, void* stream);
+
 /* Temporal sliding window of models (Sec. 4.2: the most recent time steps
  * stay available as trained models; when the window is full the oldest
  * step is dropped). A step holds one model per partition (n_parts boxes,

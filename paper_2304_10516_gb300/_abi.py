@@ -31,6 +31,7 @@ EXPORTS = [
     "dvnr_error_stats_noalloc", "dvnr_export_fp16", "dvnr_import_fp16", "dvnr_render_inr",
     "dvnr_adaptive_encoding", "dvnr_freeze", "dvnr_window_create", "dvnr_window_destroy",
     "dvnr_window_push", "dvnr_window_range", "dvnr_window_model", "dvnr_window_bytes",
+    "dvnr_render_in_frame", "dvnr_composite",
 ]
 
 
@@ -102,6 +103,9 @@ _SIGS = {
     "dvnr_render": ([_P, C.c_int32, C.POINTER(dvnr_tf), C.c_int32, C.c_int32, C.c_int32, _P, _P],
                     C.c_int),
     "dvnr_freeze": ([_P, _P], C.c_int),
+    "dvnr_render_in_frame": ([_P, C.c_int32, _P, _P, C.POINTER(dvnr_tf), C.c_int32, C.c_int32,
+                              C.c_int32, C.c_int32, _P, _P], C.c_int),
+    "dvnr_composite": ([_P, _P, C.c_int32, C.c_int32, C.c_int32, _P, _P], C.c_int),
     "dvnr_window_create": ([_P, C.c_int32, _P, _P, C.c_int32, C.c_uint64, _P], C.c_int),
     "dvnr_window_destroy": ([_P], None),
     "dvnr_window_push": ([_P, _P, _P, _P, _P, _P], C.c_int),

@@ -737,18 +737,35 @@ dvnr_status dvnr_decode_grid(dvnr_model m, float* out_dev, void* stream) {
   return fp32_decode_unit(m, nullptr, nullptr, n, 1, out_dev, (cudaStream_t)stream);
 }
 
-dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w, int32_t h,
-                        int32_t spr, float* rgba_dev, void* stream) {
-  g_err[0] = 0;
+static dvnr_status check_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w,
+                                int32_t h, int32_t spr, float* rgba_dev) {
   if (n < 1 || !models || !tf || !rgba_dev) return fail(DVNR_E_INVALID, "NULL argument or n < 1");
   if (w < 1 || h < 1 || spr < 1) return fail(DVNR_E_INVALID, "w, h, spr must be >= 1");
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!models[i]) return fail(DVNR_E_INVALID, "model %d is NULL", i);
+    if (models[i]->device != models[0]->device) return fail(DVNR_E_INVALID, "models on different devices");
+  }
+  return DVNR_OK;
+}
+
+static void union_frame(const dvnr_model* models, int32_t n, float lo[3], float hi[3]) {
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = 1e30f;
+    hi[a] = -1e30f;
+    for (int i = 0; i < n; ++i) {
+      lo[a] = std::min(lo[a], (float)models[i]->box.lo[a]);
+      hi[a] = std::max(hi[a], (float)models[i]->box.hi[a]);
+    }
+  }
+}
+
+static dvnr_status render_grid(const dvnr_model* models, int32_t n, const float lo[3], const float hi[3],
+                               const dvnr_tf* tf, int32_t w, int32_t h, int32_t spr, float* rgba_dev,
+                               void* stream) {
   dvnr_status rc = use_device(models[0]);
   if (rc != DVNR_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<RenderBlock> blocks((size_t)n);
-  float lo[3] = {1e30f, 1e30f, 1e30f}, hi[3] = {-1e30f, -1e30f, -1e30f};
   for (int i = 0; i < n; ++i) {
     dvnr_model m = models[i];
     const size_t ne = (size_t)((m->box.hi[0] - m->box.lo[0]) * (m->box.hi[1] - m->box.lo[1]) *
@@ -769,8 +786,6 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, 
       b.lo[a] = (float)m->box.lo[a];
       b.hi[a] = (float)m->box.hi[a];
       b.e[a] = (int32_t)(m->box.hi[a] - m->box.lo[a]);
-      lo[a] = std::min(lo[a], b.lo[a]);
-      hi[a] = std::max(hi[a], b.hi[a]);
     }
     b.pad = 0;
     b.grid = m->grid_ws;
@@ -787,22 +802,68 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, 
   return rc;
 }
 
-dvnr_status dvnr_render_inr(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w,
-                            int32_t h, int32_t spr, float* rgba_dev, void* stream) {
-  g_err[0] = 0;
-  if (n < 1 || !models || !tf || !rgba_dev) return fail(DVNR_E_INVALID, "NULL argument or n < 1");
-  if (w < 1 || h < 1 || spr < 1) return fail(DVNR_E_INVALID, "w, h, spr must be >= 1");
+static dvnr_status check_inr(const dvnr_model* models, int32_t n) {
   for (int i = 0; i < n; ++i) {
-    if (!models[i]) return fail(DVNR_E_INVALID, "model %d is NULL", i);
-    if (models[i]->device != models[0]->device) return fail(DVNR_E_INVALID, "models on different devices");
     if (models[i]->precision != models[0]->precision)
       return fail(DVNR_E_INVALID, "model %d: all models must use one precision", i);
     if (models[0]->precision == DVNR_FP16 && !mp_supported(models[i]))
       return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
   }
-  dvnr_status rc = use_device(models[0]);
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w, int32_t h,
+                        int32_t spr, float* rgba_dev, void* stream) {
+  g_err[0] = 0;
+  dvnr_status rc = check_render(models, n, tf, w, h, spr, rgba_dev);
   if (rc != DVNR_OK) return rc;
-  return render_inr(models, n, *tf, w, h, spr, rgba_dev, (cudaStream_t)stream);
+  float lo[3], hi[3];
+  union_frame(models, n, lo, hi);
+  return render_grid(models, n, lo, hi, tf, w, h, spr, rgba_dev, stream);
+}
+
+dvnr_status dvnr_render_in_frame(const dvnr_model* models, int32_t n, const int64_t frame_lo[3],
+                                 const int64_t frame_hi[3], const dvnr_tf* tf, int32_t w, int32_t h,
+                                 int32_t spr, int32_t from_network, float* rgba_dev, void* stream) {
+  g_err[0] = 0;
+  dvnr_status rc = check_render(models, n, tf, w, h, spr, rgba_dev);
+  if (rc != DVNR_OK) return rc;
+  if (!frame_lo || !frame_hi) return fail(DVNR_E_INVALID, "NULL frame");
+  float lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    if (frame_hi[a] <= frame_lo[a]) return fail(DVNR_E_INVALID, "frame must have hi > lo on every axis");
+    lo[a] = (float)frame_lo[a];
+    hi[a] = (float)frame_hi[a];
+  }
+  if (!from_network) return render_grid(models, n, lo, hi, tf, w, h, spr, rgba_dev, stream);
+  if ((rc = check_inr(models, n)) != DVNR_OK) return rc;
+  if ((rc = use_device(models[0])) != DVNR_OK) return rc;
+  return render_inr(models, n, lo, hi, *tf, w, h, spr, rgba_dev, (cudaStream_t)stream);
+}
+
+dvnr_status dvnr_composite(const float* const* rgba_dev, const double* depth_host, int32_t n, int32_t w,
+                           int32_t h, float* out_dev, void* stream) {
+  g_err[0] = 0;
+  if (n < 1 || !rgba_dev || !depth_host || !out_dev) return fail(DVNR_E_INVALID, "NULL argument or n < 1");
+  if (w < 1 || h < 1) return fail(DVNR_E_INVALID, "w, h must be >= 1");
+  for (int i = 0; i < n; ++i)
+    if (!rgba_dev[i]) return fail(DVNR_E_INVALID, "image %d is NULL", i);
+  std::vector<int> order((size_t)n);
+  for (int i = 0; i < n; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return depth_host[a] < depth_host[b]; });
+  return composite(rgba_dev, order.data(), n, (int64_t)w * h, out_dev, (cudaStream_t)stream);
+}
+
+dvnr_status dvnr_render_inr(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w,
+                            int32_t h, int32_t spr, float* rgba_dev, void* stream) {
+  g_err[0] = 0;
+  dvnr_status rc = check_render(models, n, tf, w, h, spr, rgba_dev);
+  if (rc != DVNR_OK) return rc;
+  if ((rc = check_inr(models, n)) != DVNR_OK) return rc;
+  if ((rc = use_device(models[0])) != DVNR_OK) return rc;
+  float lo[3], hi[3];
+  union_frame(models, n, lo, hi);
+  return render_inr(models, n, lo, hi, *tf, w, h, spr, rgba_dev, (cudaStream_t)stream);
 }
 
 dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n, double* out_host,

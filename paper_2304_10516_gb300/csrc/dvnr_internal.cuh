@@ -357,8 +357,12 @@ bool same_arch(const dvnr_model a, const dvnr_model b);
 // Direct INR ray-marching (render_inr.cu): same camera and transfer function
 // as launch_render, values from the models' networks at the ray samples.
 // All models share one precision; FP16 models also one architecture.
-dvnr_status render_inr(const dvnr_model* models, int n, const dvnr_tf& tf, int w, int h, int spr,
-                       float* rgba, cudaStream_t s);
+dvnr_status render_inr(const dvnr_model* models, int n, const float* frame_lo, const float* frame_hi,
+                       const dvnr_tf& tf, int w, int h, int spr, float* rgba, cudaStream_t s);
+// Sort-last blend (render_inr.cu): images rgba[order[0]] (front) ..
+// rgba[order[n-1]] (back), npix float4 pixels each, into out; synchronises.
+dvnr_status composite(const float* const* rgba, const int* order, int n, int64_t npix, float* out,
+                      cudaStream_t s);
 dvnr_status launch_state_reset(ModelState* st, float loss_scale, cudaStream_t s);
 dvnr_status launch_state_reset_scale(ModelState* st, float loss_scale, cudaStream_t s);
 dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_batch, float* grad_out,

@@ -311,17 +311,13 @@ int first_at_or_after(int n, float edge, Fn coord) {
 
 }  // namespace
 
-dvnr_status render_inr(const dvnr_model* models, int n, const dvnr_tf& tf, int w, int h, int spr,
-                       float* rgba, cudaStream_t s) {
+dvnr_status render_inr(const dvnr_model* models, int n, const float* frame_lo, const float* frame_hi,
+                       const dvnr_tf& tf, int w, int h, int spr, float* rgba, cudaStream_t s) {
   const bool fp16 = models[0]->precision == DVNR_FP16;
   InrFrame fr{};
   for (int a = 0; a < 3; ++a) {
-    fr.lo[a] = 1e30f;
-    fr.hi[a] = -1e30f;
-    for (int i = 0; i < n; ++i) {
-      fr.lo[a] = std::min(fr.lo[a], (float)models[i]->box.lo[a]);
-      fr.hi[a] = std::max(fr.hi[a], (float)models[i]->box.hi[a]);
-    }
+    fr.lo[a] = frame_lo[a];
+    fr.hi[a] = frame_hi[a];
   }
   fr.w = w;
   fr.h = h;
@@ -487,6 +483,46 @@ dvnr_status render_inr(const dvnr_model* models, int n, const dvnr_tf& tf, int w
   cudaFreeAsync(part, s);
   cudaFreeAsync(dblocks, s);
   if (rc == DVNR_OK) DVNR_CUDA(cudaStreamSynchronize(s));  // the host block table is released
+  return rc;
+}
+
+namespace {
+
+// Sort-last blend of n premultiplied RGBA images, imgs[0] frontmost.
+__global__ void k_composite(const float4* const* __restrict__ imgs, int n, int64_t npix,
+                            float4* __restrict__ out) {
+  const int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = 0; i < n; ++i) {
+    const float4 c = imgs[i][pix];
+    const float t = 1.f - acc.w;
+    acc.x += t * c.x;
+    acc.y += t * c.y;
+    acc.z += t * c.z;
+    acc.w += t * c.w;
+  }
+  out[pix] = acc;
+}
+
+}  // namespace
+
+dvnr_status composite(const float* const* rgba, const int* order, int n, int64_t npix, float* out,
+                      cudaStream_t s) {
+  std::vector<const float4*> ptrs((size_t)n);
+  for (int i = 0; i < n; ++i) ptrs[(size_t)i] = reinterpret_cast<const float4*>(rgba[order[i]]);
+  const float4** d = nullptr;
+  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), (size_t)n * sizeof(float4*), s));
+  DVNR_CUDA(cudaMemcpyAsync(d, ptrs.data(), (size_t)n * sizeof(float4*), cudaMemcpyHostToDevice, s));
+  dvnr_status rc = DVNR_OK;
+  {
+    ProfScope ps("composite", s);
+    k_composite<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(d, n, npix, reinterpret_cast<float4*>(out));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) rc = cuda_status(e, "composite");
+  cudaFreeAsync(d, s);
+  if (rc == DVNR_OK) DVNR_CUDA(cudaStreamSynchronize(s));  // the host pointer table is released
   return rc;
 }
 

@@ -332,6 +332,41 @@ def render_inr(models, tf, w, h, spr, out=None, stream=None):
     return out
 
 
+def render_in_frame(models, frame_lo, frame_hi, tf, w, h, spr, from_network=False, out=None,
+                    stream=None):
+    """Render `models` with the camera spanning [frame_lo, frame_hi) (the
+    global domain): images of disjoint partitions rendered apart composite
+    into the image of all of them."""
+    import torch
+
+    n = len(models)
+    hs = (C.c_void_p * n)(*[m.handle for m in models])
+    if out is None:
+        out = torch.empty((h, w, 4), dtype=torch.float32, device="cuda")
+    lo = (C.c_int64 * 3)(*[int(v) for v in frame_lo])
+    hi = (C.c_int64 * 3)(*[int(v) for v in frame_hi])
+    A.call("dvnr_render_in_frame", C.cast(hs, C.c_void_p), n, lo, hi, C.byref(tf), w, h, spr,
+           1 if from_network else 0, _ptr(out), _stream(stream))
+    return out
+
+
+def composite(images, depths, out=None, stream=None):
+    """Sort-last blend of premultiplied RGBA images (h, w, 4) in increasing
+    depth (front first)."""
+    import torch
+
+    n = len(images)
+    h, w = images[0].shape[0], images[0].shape[1]
+    imgs = [im.contiguous() for im in images]
+    ptrs = (C.c_void_p * n)(*[im.data_ptr() for im in imgs])
+    dep = (C.c_double * n)(*[float(d) for d in depths])
+    if out is None:
+        out = torch.empty((h, w, 4), dtype=torch.float32, device=imgs[0].device)
+    A.call("dvnr_composite", C.cast(ptrs, C.c_void_p), C.cast(dep, C.c_void_p), n, w, h, _ptr(out),
+           _stream(stream))
+    return out
+
+
 def error_stats(a, b, stream=None):
     """(sum of squared differences, max abs difference) in FP64 on the device."""
     out = (C.c_double * 2)()

@@ -1,9 +1,12 @@
 """Distribution of partition models over ranks (one process per GPU).
 
 The models of different partitions never exchange data while training
-(Sec. 3.1 of the paper), so the only multi-rank logic is which rank trains
-which partition and how a timing is agreed on: there is no collective on the
-data path.
+(Sec. 3.1 of the paper): which rank trains which partition and how a timing
+is agreed on need no data-path collective. The exchanges of the paper's
+visualisation pipeline are here too: sort-last compositing of the ranks'
+images (Sec. 4.3: gather, then blend in depth order with the library's
+dvnr_composite) and the global error (Sec. 5: sums of squared errors and
+voxel counts reduced in FP64).
 """
 from __future__ import annotations
 
@@ -43,3 +46,58 @@ def max_over_ranks(value: float) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _device_for(tensor_device):
+    import torch
+    import torch.distributed as dist
+
+    if dist.get_backend() == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
+def gather_images(rgba, depth: float):
+    """All-gather every rank's image (h, w, 4) and the depth of its partition
+    (e.g. its box's lo.z); returns (images, depths) in rank order on every
+    rank. Images travel on the backend's device (GPU for NCCL, host for
+    gloo) and come back on the device of `rgba`."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return [rgba], [float(depth)]
+    world = dist.get_world_size()
+    dev = _device_for(rgba.device)
+    x = rgba.contiguous().to(dev)
+    bufs = [torch.empty_like(x) for _ in range(world)]
+    dist.all_gather(bufs, x)
+    d = torch.tensor([float(depth)], dtype=torch.float64, device=dev)
+    dbufs = [torch.empty_like(d) for _ in range(world)]
+    dist.all_gather(dbufs, d)
+    return [b.to(rgba.device) for b in bufs], [float(v.item()) for v in dbufs]
+
+
+def composite_sort_last(rgba, depth: float, stream=None):
+    """The image of all ranks' partitions: gather the ranks' images and blend
+    them front to back on this rank's GPU (library kernel)."""
+    from . import model as dv
+
+    images, depths = gather_images(rgba, depth)
+    return dv.composite(images, depths, stream=stream)
+
+
+def global_psnr(sse: float, count: int, value_range: float = 1.0):
+    """PSNR over the voxels of all ranks (Sec. 5): the squared errors and
+    voxel counts are summed over ranks in FP64 first (voxel-weighted)."""
+    import math
+
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(sse), float(count)], dtype=torch.float64)
+    if dist.is_available() and dist.is_initialized():
+        t = t.to(_device_for(t.device))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    s, n = float(t[0].item()), float(t[1].item())
+    return 20 * math.log10(value_range) - 10 * math.log10(s / n), s, n
