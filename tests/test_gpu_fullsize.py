@@ -116,3 +116,57 @@ def test_fullsize_render_inr_sampled_pixels(setup, precision):
     np.testing.assert_allclose(img[pix, 3], want[:, 3], atol=bound, rtol=0)
     np.testing.assert_allclose(img[pix, :3], want[:, :3], atol=3 * bound, rtol=0)
     assert np.isfinite(img).all() and img[:, 3].max() <= 1.0 + 1e-6
+
+
+@pytest.mark.parametrize("precision", [1, 0], ids=["fp16", "fp32"])
+def test_fullsize_decode_and_grid_march_sampled(setup, precision):
+    # the benchmark's decode (256^3 owned voxels) and decoded-grid ray-march
+    # (1024 x 1024 x 512) on sampled voxels and pixels: the oracle decodes the
+    # sampled voxels, and for the sampled rays every voxel they interpolate
+    # (2 x 2 columns through the volume); all other voxels are NaN in the
+    # oracle's grid, so a ray that touched one would fail
+    import test_gpu_render_inr as R
+
+    orc, dv, c, oc, vol, theta = setup
+    mixed = precision == 1
+    m = dv.Model((0, 0, 0), (256, 256, 256), 0,
+                 dv.EncodingConfig(c["L"], c["F"], c["log2T"], c["base"], c["growth"]),
+                 dv.MLPConfig(c["width"], c["hidden"]), seed=0)
+    m.set_weights(theta)
+    m.set_precision(precision)
+    grid = m.decode_grid().cpu().numpy()
+    n = 256
+    gc = np.array([orc.grid_coord(j, n) for j in range(n)], dtype=np.uint32)
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, n, size=(3000, 3))
+    want = orc.decode_unit(oc, theta.astype(np.float64), gc[idx], 0.0, 1.0, mixed=mixed)
+    got = grid[idx[:, 2], idx[:, 1], idx[:, 0]]
+    dv_tol = 2e-3 * max(1.0, np.abs(want).max()) if mixed else 1e-5
+    err = np.abs(got - want).max()
+    assert err <= dv_tol, err
+    # grid march of sampled pixels
+    w = h = 1024
+    spr = 512
+    img = dv.render([m], dv.make_tf(**R.TF), w, h, spr).cpu().numpy().reshape(-1, 4)
+    pix = rng.choice(w * h, size=24, replace=False)
+    og = np.full((n, n, n), np.nan)
+    for p_ in pix:
+        px, py = p_ % w, p_ // w
+        cols = []
+        for q, e in ((px, w), (py, h)):
+            X = -0.5 + (q + 0.5) * n / e
+            b = min(max(int(np.floor(min(max(X, 0.0), n - 1))), 0), n - 2)
+            cols.append((b, b + 1))
+        for x in cols[0]:
+            for y in cols[1]:
+                mm = np.stack([np.full(n, gc[x]), np.full(n, gc[y]), gc], 1).astype(np.uint32)
+                og[:, y, x] = orc.decode_unit(oc, theta.astype(np.float64), mm, 0.0, 1.0, mixed=mixed)
+    ref = orc.render([og], [(0, 0, 0)], [(n, n, n)], R._tf_list(), w, h, spr).reshape(-1, 4)[pix]
+    assert np.isfinite(ref).all()
+    used = np.isfinite(og)
+    err_rays = np.abs(grid[used] - og[used]).max()
+    assert err_rays <= dv_tol, err_rays
+    # the march interpolates decoded values, each within err_rays of the oracle's
+    bound = R.TF["alpha_max"] * spr * max(err_rays, 1e-7) / (R.TF["v_hi"] - R.TF["v_lo"]) + 1e-5
+    np.testing.assert_allclose(img[pix, 3], ref[:, 3], atol=bound, rtol=0)
+    np.testing.assert_allclose(img[pix, :3], ref[:, :3], atol=3 * bound, rtol=0)
