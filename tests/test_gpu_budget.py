@@ -192,7 +192,8 @@ def test_fp16_losses_cover_every_tile_after_a_model_leaves(dv, orc):
     qtab = orc.quantile_table(0.005)
     for slot in (0, 2):
         assert s[slot]["iter"] == K and s[slot]["stopped"] == 0
-        np.testing.assert_array_equal(models[slot].get_weights(), th0[slot])
+        # (an Adam step of lr 1e-30 moves only parameters within ~1e-28 of zero)
+        np.testing.assert_allclose(models[slot].get_weights(), th0[slot], rtol=1e-6, atol=1e-25)
         v = vols[slot].cpu().numpy()
         coords = orc.sample(5, slot, K - 1, B, 0.0, qtab)
         t = orc.targets(v, coords, float(v.min()), float(v.max()))
