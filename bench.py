@@ -613,7 +613,8 @@ def render_inr_leg(model, tf, img_grid, grid, stream):
     return {"value": w * h * spr / (ms / 1e3), "unit": "ray samples/s (network inferences/s)",
             "ms": ms, "psnr_vs_grid_march_db": 10 * math.log10(1.0 / max(mse, 1e-30)),
             "max_abs_vs_grid_march": float((img - img_grid).abs().max()),
-            "work_bytes": w * h * 16, "grid_bytes": grid.numel() * 4,
+            "work_bytes": w * h * 16 + min(w * h, (1 << 24) // spr) * spr * 4,
+            "grid_bytes": grid.numel() * 4,
             "model_bytes_fp16": model.n_params * 2}
 
 

@@ -369,12 +369,12 @@ dvnr_status dvnr_window_bytes(dvnr_window w, int64_t* model_bytes, int64_t* devi
  * block's network evaluated at the sample position (mapped into the block's
  * unit domain and clamped to it, as dvnr_decode_points), de-normalised. The
  * boxes must not overlap. All models must use one precision (the training
- * precision, or dvnr_set_precision); FP16 models of different encoding or
- * MLP configuration are marched by one launch per configuration. Work
- * memory: 16 bytes per (pixel, block) pair whose
- * ray crosses the block (FP32 models: plus 16 bytes per sample of a chunk
- * of at most 2^24 samples), allocated stream-ordered and released before
- * return. Synchronises the stream. Errors: DVNR_E_INVALID
+ * precision, or dvnr_set_precision); models may differ in encoding and MLP
+ * configuration. The samples are streamed block by block through the
+ * block's decoder in chunks of at most 2^24. Work memory: 16 bytes per
+ * (pixel, block) pair whose ray crosses the block plus 4 bytes per sample
+ * of a chunk (FP32 models: 16), allocated stream-ordered and released
+ * before return. Synchronises the stream. Errors: DVNR_E_INVALID
  * (arguments, mixed precisions or configurations), DVNR_E_UNSUPPORTED,
  * DVNR_E_CUDA.                                                               */
 dvnr_status dvnr_render_inr(const dvnr_model* models, int32_t n, const dvnr_tf* tf,

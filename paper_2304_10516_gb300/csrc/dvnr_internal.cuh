@@ -283,6 +283,32 @@ __device__ __forceinline__ float volume_trilinear(const float* __restrict__ vol,
   return vol_interp(vol_fetch(vol, nx, ny, nz, m));
 }
 
+// Ray lattice of direct volume rendering (Sec. 4.3 reading): orthographic
+// rays along +z through pixel centres over the frame [lo - 1/2, hi - 1/2),
+// spr samples at the centres of spr equal steps in z. A block owns the
+// pixels px0 .. px0+npx-1, py0 .. py0+npy-1 whose ray centre lies in its box
+// and the samples k0 .. k0+nk-1 inside it; its rays are numbered row-major
+// over that footprint. Positions use these single-precision expressions on
+// the host and the device alike.
+struct RayFrame {
+  float lo[3], hi[3];
+  int32_t w, h, spr;
+};
+struct RayBlock {
+  float origin[3];  // global coordinate of the block's stored voxel 0 (lo - ghost)
+  int32_t nstore[3];
+  int32_t px0, npx, py0, npy, k0, nk;
+};
+__host__ __device__ __forceinline__ float frame_x(const RayFrame& f, int px) {
+  return (f.lo[0] - 0.5f) + ((px + 0.5f) * (f.hi[0] - f.lo[0])) / (float)f.w;
+}
+__host__ __device__ __forceinline__ float frame_y(const RayFrame& f, int py) {
+  return (f.lo[1] - 0.5f) + ((py + 0.5f) * (f.hi[1] - f.lo[1])) / (float)f.h;
+}
+__host__ __device__ __forceinline__ float frame_z(const RayFrame& f, int k) {
+  return (f.lo[2] - 0.5f) + ((k + 0.5f) * (f.hi[2] - f.lo[2])) / (float)f.spr;
+}
+
 __device__ __forceinline__ void value_range(const ModelState* st, float& vmin, float& inv_range) {
   vmin = ordered_to_float(st->enc_min);
   const float vmax = ordered_to_float(st->enc_max);

@@ -96,8 +96,11 @@ struct MpDecodeParams {
   const ModelState* st;
   int64_t n, n_tiles;
   const float* xyz;
-  int grid_mode;
+  int grid_mode;  // 0: xyz points, 1: the owned grid, 2: ray lattice (depth-major)
   int64_t e[3], nstore[3];
+  RayFrame rf;     // grid_mode 2: the samples of rays r0 .. r0+nr-1 of block rb,
+  RayBlock rb;     // point i = sample k0 + i / nr of ray r0 + i % nr
+  int64_t r0, nr;
   int32_t ghost;
   float origin[3];
   float* out;
@@ -669,7 +672,13 @@ __global__ void __launch_bounds__(kTile) k_mp_decode(const __grid_constant__ MpD
     const bool valid = i < p.n;
     uint3 m = make_uint3(0u, 0u, 0u);
     if (valid) {
-      if (p.grid_mode) {
+      if (p.grid_mode == 2) {
+        const int64_t k = i / p.nr, ray = p.r0 + (i - k * p.nr);
+        const int px = p.rb.px0 + (int)(ray % p.rb.npx), py = p.rb.py0 + (int)(ray / p.rb.npx);
+        m = make_uint3(dec_unit_to_fixed(frame_x(p.rf, px), p.rb.origin[0], p.rb.nstore[0]),
+                       dec_unit_to_fixed(frame_y(p.rf, py), p.rb.origin[1], p.rb.nstore[1]),
+                       dec_unit_to_fixed(frame_z(p.rf, p.rb.k0 + (int)k), p.rb.origin[2], p.rb.nstore[2]));
+      } else if (p.grid_mode) {
         const int64_t x = i % p.e[0], y = (i / p.e[0]) % p.e[1], z = i / (p.e[0] * p.e[1]);
         m = make_uint3(dec_grid_fixed(x + p.ghost, p.nstore[0]), dec_grid_fixed(y + p.ghost, p.nstore[1]),
                        dec_grid_fixed(z + p.ghost, p.nstore[2]));
@@ -1302,8 +1311,18 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
   return rc;
 }
 
+dvnr_status mp_decode_rays(dvnr_model m, const RayFrame& rf, const RayBlock& rb, int64_t r0, int64_t nr,
+                           float* out, cudaStream_t s) {
+  return mp_decode_impl(m, nullptr, nr * rb.nk, 2, &rf, &rb, r0, nr, out, s);
+}
+
 dvnr_status mp_decode(dvnr_model m, const float* xyz, int64_t n, int grid_mode, float* out,
                       cudaStream_t s) {
+  return mp_decode_impl(m, xyz, n, grid_mode, nullptr, nullptr, 0, 0, out, s);
+}
+
+dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_mode, const RayFrame* rf,
+                           const RayBlock* rb, int64_t r0, int64_t nr, float* out, cudaStream_t s) {
   if (n <= 0) return DVNR_OK;
   MpLayout lay;
   if (!make_layout(m, false, lay)) {
@@ -1329,6 +1348,12 @@ dvnr_status mp_decode(dvnr_model m, const float* xyz, int64_t n, int grid_mode, 
   }
   p.ghost = m->box.ghost;
   p.out = out;
+  if (rf) {
+    p.rf = *rf;
+    p.rb = *rb;
+    p.r0 = r0;
+    p.nr = nr;
+  }
   const int W = m->mlp.width, F = m->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, false, lay.smem_bytes);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p.n_tiles, (int64_t)sm_count() * lay.ctas_per_sm));

@@ -32,5 +32,11 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
 // FP16 inference: xyz points (grid_mode 0) or the owned grid (grid_mode 1).
 dvnr_status mp_decode(dvnr_model m, const float* xyz, int64_t n, int grid_mode, float* out,
                       cudaStream_t s);
+// FP16 inference at the samples of rays r0 .. r0+nr-1 of block rb of the
+// ray lattice rf, depth-major: out[(k - k0) nr + ray - r0] (nr * rb.nk values).
+dvnr_status mp_decode_rays(dvnr_model m, const RayFrame& rf, const RayBlock& rb, int64_t r0, int64_t nr,
+                           float* out, cudaStream_t s);
+dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_mode, const RayFrame* rf,
+                           const RayBlock* rb, int64_t r0, int64_t nr, float* out, cudaStream_t s);
 
 }  // namespace dvnr
