@@ -222,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
     import ctypes as C
 
     kern = {}
-    names = ["train_fused_fp16", "mp_reduce", "adam", "minmax", "fp32_sample_encode",
+    names = ["train_fused_fp16", "mp_schedule", "adam", "minmax", "fp32_sample_encode",
              "fp32_gemm", "fp32_out_loss", "fp32_scatter"]
     for n in names:
         tms, cnt = C.c_double(), C.c_int64()
@@ -436,7 +436,7 @@ def run_blocks(args, rank, world, local_rank):
     hbm, have = _peaks()
     A.call("dvnr_profile_enable", 1)
     dv.train(models, vols, cfg(min(args.steps, 20)))
-    kern = _profile(A, ["train_fused_fp16", "mp_reduce", "adam", "minmax"])
+    kern = _profile(A, ["train_fused_fp16", "mp_schedule", "adam", "minmax"])
     A.call("dvnr_profile_enable", 0)
     res["roofline"] = _roofline(kern, w, models[0].n_params * n, n * w["batch"], hbm, have)
     # full training from fresh models, then decode and PSNR over owned voxels

@@ -43,7 +43,7 @@ namespace {
 #endif
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
-[[maybe_unused]] constexpr int kTrainKernelRevision = 8;
+[[maybe_unused]] constexpr int kTrainKernelRevision = 9;
 
 struct MpModel {
   const __half* theta16;
@@ -72,14 +72,11 @@ struct MpParams {
   float* dbg_dx0;
   float* dbg_tgt;
   uint32_t* dbg_coords;
-  // per-CTA partial weight gradients and loss, reduced by k_mp_reduce
-  float* partial;
-  int32_t n_mlp, part_stride, slots_per_cta;
   // models are trained in waves of models_per_wave (wave_tiles tiles): every
   // CTA walks its share of wave 0, then of wave 1, ..., so that the tables and
   // gradients in use at any time stay within L2
   int64_t wave_tiles;
-  int32_t n_waves, models_per_wave, slots_per_wave;
+  int32_t n_waves, models_per_wave;
   // models of the step: sched[0] = n_active, sched[1 + a] = index of the
   // a-th active model, sched[1 + n_models + m] = position of model m (-1 when
   // inactive), written by k_mp_schedule; nullptr = all n_models take part
@@ -213,7 +210,6 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
   uint32_t phase = 0;
 
   int cur = -1;
-  size_t cur_slot = 0;
   bool first_tile = true;
   MpModel md{};
   SampleParams sp;
@@ -234,11 +230,12 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     return *abort_flag == 0u;
   };
 
-  // hand the run's weight gradients and loss of the current model to this
-  // CTA's partial slot (plain stores; k_mp_reduce sums the slots)
+  // add the run's weight gradients and loss of the current model to the
+  // model's MLP gradient and loss sum (16-byte vector reductions; every CTA
+  // whose run touched the model adds its share, Adam clears them)
   auto flush = [&]() {
     umma::fence_after_sync();
-    float* part = p.partial + ((size_t)blockIdx.x * p.slots_per_cta + cur_slot) * p.part_stride;
+    float* part = md.grad + p.w_off[0];
     if (warp * 32 < W) {
       const int r = warp * 32 + lane;  // output row of the layer
       for (int k = 0; k < H; ++k) {
@@ -249,9 +246,8 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
           umma::ld16(tl + p.lay.dw_col[k] + c, v);
           umma::ld_wait();
           if (r < W) {
-            float4* dst = reinterpret_cast<float4*>(g + (size_t)r * in + c);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            for (int j = 0; j < 4; ++j) red_add<4>(g + (size_t)r * in + c + 4 * j, v + 4 * j);
           }
         }
       }
@@ -271,7 +267,10 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     __syncthreads();
     if (tid <= W) {
       const float t = s_red[tid] + s_red[(W + 1) + tid] + s_red[2 * (W + 1) + tid] + s_red[3 * (W + 1) + tid];
-      part[tid < W ? (p.w_off[H] - p.w_off[0]) + tid : (int64_t)p.n_mlp] = t;
+      if (tid < W)
+        atomicAdd(part + (p.w_off[H] - p.w_off[0]) + tid, t);
+      else
+        atomicAdd(&md.st->loss_sum, t);
     }
     umma::fence_before_sync();
     __syncthreads();
@@ -284,7 +283,6 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
   const int64_t Tw = p.wave_tiles < T_act - wb ? p.wave_tiles : T_act - wb;
   const int64_t g_begin = wb + (Tw * blockIdx.x) / gridDim.x;
   const int64_t g_end = wb + (Tw * (blockIdx.x + 1)) / gridDim.x;
-  const int first_pos = (int)(g_begin / p.tiles_per_model);
   for (int64_t g = g_begin; g < g_end; ++g) {
     const int pos = (int)(g / p.tiles_per_model);
     const int tile = (int)(g - (int64_t)pos * p.tiles_per_model);
@@ -292,7 +290,6 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     if (model != cur) {
       if (cur >= 0) flush();
       cur = model;
-      cur_slot = (size_t)wv * p.slots_per_wave + (size_t)(pos - first_pos);
       md = p.models[model];
       sp.model = md.slot;
       iter = p.explicit_iter ? p.iter : md.st->iter;
@@ -527,78 +524,6 @@ teardown:
   __syncthreads();
   umma::fence_after_sync();
   if (warp == 0) umma::tmem_dealloc(tmem, p.lay.tmem_cols);
-}
-
-// Sum the per-CTA partial weight gradients (and losses) of every model. In
-// wave w, CTA c covered the wave's tiles [Tw c / G, Tw (c+1) / G) and wrote
-// model m into slot w * slots_per_wave + (m - first model of its chunk);
-// CTAs whose chunk is empty or misses the model wrote nothing for it. A block
-// sums 32 consecutive entries (one per lane, coalesced) with its 8 warps
-// splitting the CTAs, then combines the warps in shared memory. The MLP
-// gradients are zero before this kernel (Adam clears them), so the sum is
-// stored.
-constexpr int kReduceWarps = 8;
-
-__global__ void __launch_bounds__(32 * kReduceWarps)
-    k_mp_reduce(const MpModel* __restrict__ models, const float* __restrict__ partial,
-                int part_stride, int slots, int n_mlp, int64_t w_off0, int64_t tpm, int n_models,
-                const int32_t* __restrict__ sched, int64_t G, int64_t wave_tiles,
-                int models_per_wave, int slots_per_wave) {
-  const int m = blockIdx.y;
-  // the model's position among the step's active models (k_mp_train numbers
-  // tiles over active models only); an inactive model has no partials
-  const int a = sched ? sched[1 + n_models + m] : m;
-  if (a < 0) return;
-  const int64_t T = (int64_t)(sched ? sched[0] : n_models) * tpm;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int j = blockIdx.x * 32 + lane;
-  // the model's wave and its tiles relative to the wave (tile counts stay
-  // below 2^32 / G, so 32-bit products and quotients suffice)
-  const int wv = a / models_per_wave, m_rel = a - wv * models_per_wave;
-  const int64_t wb = (int64_t)wv * wave_tiles;
-  const uint32_t Tw = (uint32_t)(wave_tiles < T - wb ? wave_tiles : T - wb);
-  const uint32_t G32 = (uint32_t)G, tpm32 = (uint32_t)tpm;
-  const uint32_t t0 = (uint32_t)m_rel * tpm32, t1 = t0 + tpm32;
-  // CTAs whose chunk starts before t1 and ends after t0
-  uint32_t c_lo = (uint32_t)(((uint64_t)t0 * G32) / Tw);
-  while (c_lo > 0 && (Tw * c_lo) / G32 > t0) --c_lo;
-  while (c_lo < G32 && (Tw * (c_lo + 1)) / G32 <= t0) ++c_lo;
-  uint32_t c_hi = (uint32_t)(((uint64_t)t1 * G32 + Tw - 1) / Tw);
-  if (c_hi > G32) c_hi = G32;
-  while (c_hi < G32 && (Tw * c_hi) / G32 < t1) ++c_hi;
-  while (c_hi > c_lo && (Tw * (c_hi - 1)) / G32 >= t1) --c_hi;
-  float sum = 0.f;
-  if (j <= n_mlp) {
-    const float* base = partial + (size_t)wv * slots_per_wave * part_stride + j;
-    // batches of 8 CTAs per warp: all 8 (predicated) loads are issued before
-    // any is summed, so their latencies overlap
-    constexpr int kBatch = 8;
-    for (uint32_t cb = c_lo + warp; cb < c_hi; cb += kBatch * kReduceWarps) {
-      float v[kBatch];
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) {
-        const uint32_t c = cb + (uint32_t)(u * kReduceWarps);
-        const uint32_t b = (Tw * c) / G32, e = (Tw * (c + 1)) / G32;
-        const bool ok = c < c_hi && b < e;  // an empty chunk wrote nothing
-        const size_t off = ok ? ((size_t)c * slots + (m_rel - b / tpm32)) * part_stride : 0;
-        v[u] = ok ? __ldg(base + off) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < kBatch; ++u) sum += v[u];
-    }
-  }
-  __shared__ float s_part[kReduceWarps][32];
-  s_part[warp][lane] = sum;
-  __syncthreads();
-  if (warp == 0 && j <= n_mlp) {
-    float t = 0.f;
-#pragma unroll
-    for (int w = 0; w < kReduceWarps; ++w) t += s_part[w][lane];
-    if (j < n_mlp)
-      models[m].grad[w_off0 + j] = t;
-    else
-      models[m].st->loss_sum = t;
-  }
 }
 
 // The step's active models in index order (a block-wide exclusive scan of
@@ -876,8 +801,6 @@ struct MpCache {
   MpModel* d_models = nullptr;
   AdamModelPtrs* d_adam = nullptr;
   int32_t* d_sched = nullptr;  // active-model schedule, 1 + 2 n ints
-  float* d_partial = nullptr;
-  size_t partial_cap = 0;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
@@ -890,10 +813,7 @@ struct MpCache {
     if (d_models) cudaFree(d_models);
     if (d_adam) cudaFree(d_adam);
     if (d_sched) cudaFree(d_sched);
-    if (d_partial) cudaFree(d_partial);
     if (cap) cudaStreamDestroy(cap);
-    d_partial = nullptr;
-    partial_cap = 0;
     exec = nullptr;
     graph = nullptr;
     d_models = nullptr;
@@ -929,8 +849,6 @@ MpParams base_params(const dvnr_model m, const MpLayout& lay, const dvnr_train_c
   p.key = make_uint2((uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32));
   p.qtab = m->qtab;
   p.inv_batch = 1.0f / (float)cfg->batch;
-  p.n_mlp = (int32_t)m->n_mlp;
-  p.part_stride = (int32_t)((m->n_mlp + 1 + 3) / 4 * 4);  // rows stay 16-byte aligned
   return p;
 }
 
@@ -939,12 +857,11 @@ int train_grid(const MpParams& p) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(p.total_tiles, cap));
 }
 
-// Wave schedule and partial slots: models_per_wave models share the L2 at a
+// Wave schedule: models_per_wave models share the L2 at a
 // time -- as many as fit their FP16 tables and FP32 gradients into a quarter
 // of it, but at least enough for half a tile per CTA (on the 64-block
 // workload waves of 2 models train 1.34x faster than all 64 at once); the
-// DVNR_WAVE_MODELS environment variable overrides the choice. A CTA gets
-// one partial slot per model its contiguous run of a wave touches.
+// DVNR_WAVE_MODELS environment variable overrides the choice.
 int heuristic_models_per_wave(const MpParams& p, const dvnr_model m, int n_models) {
   int l2 = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -962,11 +879,6 @@ void set_waves(MpParams& p, int n_models, int mw) {
   p.models_per_wave = mw;
   p.n_waves = (n_models + mw - 1) / mw;
   p.wave_tiles = (int64_t)mw * p.tiles_per_model;
-  const int64_t G = train_grid(p);
-  const int64_t tw = std::min(p.wave_tiles, p.total_tiles);
-  const int64_t per = (tw + G - 1) / G;
-  p.slots_per_wave = (int)((per + p.tiles_per_model - 1) / p.tiles_per_model + 1);
-  p.slots_per_cta = p.n_waves * p.slots_per_wave;
 }
 
 void set_waves(MpParams& p, const dvnr_model m, int n_models) {
@@ -976,10 +888,6 @@ void set_waves(MpParams& p, const dvnr_model m, int n_models) {
     if (v > 0) mw = v;
   }
   set_waves(p, n_models, mw);
-}
-
-size_t partial_floats(const MpParams& p) {
-  return (size_t)train_grid(p) * (size_t)p.slots_per_cta * (size_t)p.part_stride;
 }
 
 dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStream_t s) {
@@ -993,20 +901,12 @@ dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStre
     DVNR_WF_DISPATCH(W, F, launch_train_wf, p, train_grid(p), s);
   }
   DVNR_CUDA(cudaGetLastError());
-  {
-    ProfScope ps("mp_reduce", s);
-    dim3 grid((unsigned)((p.n_mlp + 1 + 31) / 32), (unsigned)n_models);
-    k_mp_reduce<<<grid, 32 * kReduceWarps, 0, s>>>(p.models, p.partial, p.part_stride, p.slots_per_cta, p.n_mlp,
-                                     p.w_off[0], p.tiles_per_model, n_models, p.sched, train_grid(p),
-                                     p.wave_tiles, p.models_per_wave, p.slots_per_wave);
-  }
-  DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;
 }
 
 // Launch-shape autotuner of the grouped training kernel: on the first call
 // for a configuration (encoding, MLP, batch, number of models) it times the
-// fused kernel and its reduction for each candidate -- CTAs per SM (as many
+// fused kernel for each candidate -- CTAs per SM (as many
 // as fit, or one) and models per wave (the heuristic, half, double) -- on the
 // call's own models and volumes, then clears what those trial runs wrote
 // (weight gradients, loss sums, overflow flags; parameters, moments and step
@@ -1027,8 +927,8 @@ std::string tune_key(const dvnr_model m, int n, const dvnr_train_cfg* cfg) {
   return buf;
 }
 
-dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, float** partial,
-                     size_t* partial_cap, TuneChoice* out, cudaStream_t s) {
+dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, TuneChoice* out,
+                     cudaStream_t s) {
   std::vector<TuneChoice> cands;
   const int h = heuristic_models_per_wave(base, models[0], n);
   for (int ctas = base.lay.ctas_per_sm; ctas >= 1; ctas = ctas > 1 ? 1 : 0) {
@@ -1043,24 +943,6 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, flo
     if (ctas == 1) break;
   }
   (void)h;
-  // scratch large enough for every candidate
-  size_t need = 0;
-  for (const auto& c : cands) {
-    MpParams q = base;
-    q.lay.ctas_per_sm = c.ctas_per_sm;
-    set_waves(q, n, c.models_per_wave);
-    need = std::max(need, partial_floats(q));
-  }
-  if (*partial_cap < need) {
-    if (*partial) {
-      DVNR_CUDA(cudaStreamSynchronize(s));
-      cudaFree(*partial);
-      *partial = nullptr;
-      *partial_cap = 0;
-    }
-    DVNR_CUDA(cudaMalloc(partial, need * sizeof(float)));
-    *partial_cap = need;
-  }
   cudaEvent_t e0, e1;
   DVNR_CUDA(cudaEventCreate(&e0));
   DVNR_CUDA(cudaEventCreate(&e1));
@@ -1071,7 +953,6 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, flo
     MpParams q = base;
     q.lay.ctas_per_sm = c.ctas_per_sm;
     set_waves(q, n, c.models_per_wave);
-    q.partial = *partial;
     if ((rc = launch_train(q, W, F, n, s)) != DVNR_OK) break;  // warm-up
     cudaEventRecord(e0, s);
     for (int r = 0; r < 3 && rc == DVNR_OK; ++r) rc = launch_train(q, W, F, n, s);
@@ -1185,7 +1066,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     if (tune && !have) {
       const int W0 = m0->mlp.width, F0 = m0->lv.F;
       DVNR_WF_DISPATCH(W0, F0, set_smem_attr, true, lay.smem_bytes);
-      dvnr_status rc = autotune(p, models, n, W0, F0, &c->d_partial, &c->partial_cap, &ch, s);
+      dvnr_status rc = autotune(p, models, n, W0, F0, &ch, s);
       if (rc != DVNR_OK) return rc;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune[key] = ch;
@@ -1209,18 +1090,6 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   c->models_per_wave = p.models_per_wave;
   c->ctas_per_sm = p.lay.ctas_per_sm;
   c->scheduled = p.sched != nullptr;
-  const size_t need = partial_floats(p);
-  if (c->partial_cap < need) {
-    if (c->d_partial) {
-      DVNR_CUDA(cudaStreamSynchronize(s));
-      cudaFree(c->d_partial);
-      c->d_partial = nullptr;
-      c->partial_cap = 0;
-    }
-    DVNR_CUDA(cudaMalloc(&c->d_partial, need * sizeof(float)));
-    c->partial_cap = need;
-  }
-  p.partial = c->d_partial;
   const int W = m0->mlp.width, F = m0->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
   auto one_step = [&](cudaStream_t st) -> dvnr_status {
@@ -1261,7 +1130,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   while (left >= G) {
     DVNR_CUDA(cudaGraphLaunch(c->exec, s));
-    count_launches((p.sched ? 4 : 3) * G);  // [schedule,] train, reduce, Adam per step
+    count_launches((p.sched ? 3 : 2) * G);  // [schedule,] train, Adam per step
     left -= G;
   }
   for (int64_t i = 0; i < left; ++i) {
@@ -1299,13 +1168,9 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
     p.dbg_y = nullptr;  // the per-sample outputs are written together
   }
   set_waves(p, m, 1);
-  float* part = nullptr;
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&part), partial_floats(p) * sizeof(float), s));
-  p.partial = part;
   const int W = m->mlp.width, F = m->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
   dvnr_status rc = launch_train(p, W, F, 1, s);
-  cudaFreeAsync(part, s);
   cudaFreeAsync(d, s);
   DVNR_CUDA(cudaStreamSynchronize(s));  // the host descriptor is released on return
   return rc;
