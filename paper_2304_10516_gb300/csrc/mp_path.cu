@@ -72,11 +72,10 @@ struct MpParams {
   float* dbg_dx0;
   float* dbg_tgt;
   uint32_t* dbg_coords;
-  // models are trained in waves of models_per_wave (wave_tiles tiles): every
-  // CTA walks its share of wave 0, then of wave 1, ..., so that the tables and
-  // gradients in use at any time stay within L2
+  // the tiles of a step are taken in waves of wave_tiles: every CTA walks
+  // its share of wave 0, then of wave 1, ..., so that the tables and
+  // gradients in use at any time stay within L2; a wave may split a model
   int64_t wave_tiles;
-  int32_t n_waves, models_per_wave;
   // models of the step: sched[0] = n_active, sched[1 + a] = index of the
   // a-th active model, sched[1 + n_models + m] = position of model m (-1 when
   // inactive), written by k_mp_schedule; nullptr = all n_models take part
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
   const int n_act = p.sched ? p.sched[0] : p.n_models;
   if (n_act <= 0) return;
   const int64_t T_act = (int64_t)n_act * p.tiles_per_model;
-  const int n_waves = (n_act + p.models_per_wave - 1) / p.models_per_wave;
+  const int n_waves = (int)((T_act + p.wave_tiles - 1) / p.wave_tiles);
 
   if (tid == 0) {
     umma::mbar_init(mbar, 1);
@@ -804,7 +803,7 @@ struct MpCache {
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
-  int models_per_wave = 0;
+  int64_t wave_tiles = 0;
   int ctas_per_sm = 0;
   bool scheduled = false;  // the captured graph launches k_mp_schedule
   void clear() {
@@ -857,11 +856,11 @@ int train_grid(const MpParams& p) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(p.total_tiles, cap));
 }
 
-// Wave schedule: models_per_wave models share the L2 at a
-// time -- as many as fit their FP16 tables and FP32 gradients into a quarter
-// of it, but at least enough for half a tile per CTA (on the 64-block
-// workload waves of 2 models train 1.34x faster than all 64 at once); the
-// DVNR_WAVE_MODELS environment variable overrides the choice.
+// Wave schedule: a wave holds about as many models as fit their FP16 tables
+// and FP32 gradients into a quarter of the L2, but at least enough tiles
+// for half a tile per CTA; the autotuner also tries waves of whole grid
+// rounds (k tiles per CTA, which keep every CTA busy when models are small)
+// and a single wave. DVNR_WAVE_MODELS=v fixes waves of v models.
 int heuristic_models_per_wave(const MpParams& p, const dvnr_model m, int n_models) {
   int l2 = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -874,11 +873,8 @@ int heuristic_models_per_wave(const MpParams& p, const dvnr_model m, int n_model
   return std::min(std::max(by_cache, by_occupancy), n_models);
 }
 
-void set_waves(MpParams& p, int n_models, int mw) {
-  mw = std::max(1, std::min(mw, n_models));
-  p.models_per_wave = mw;
-  p.n_waves = (n_models + mw - 1) / mw;
-  p.wave_tiles = (int64_t)mw * p.tiles_per_model;
+void set_wave_tiles(MpParams& p, int64_t tiles) {
+  p.wave_tiles = std::max<int64_t>(1, std::min<int64_t>(tiles, p.total_tiles));
 }
 
 void set_waves(MpParams& p, const dvnr_model m, int n_models) {
@@ -887,7 +883,7 @@ void set_waves(MpParams& p, const dvnr_model m, int n_models) {
     const int v = atoi(e);
     if (v > 0) mw = v;
   }
-  set_waves(p, n_models, mw);
+  set_wave_tiles(p, (int64_t)mw * p.tiles_per_model);
 }
 
 dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStream_t s) {
@@ -914,7 +910,7 @@ dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStre
 // DVNR_AUTOTUNE=0 keeps the heuristic; DVNR_WAVE_MODELS fixes the wave size.
 struct TuneChoice {
   int ctas_per_sm;
-  int models_per_wave;
+  int64_t wave_tiles;
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune;
@@ -935,10 +931,12 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, Tun
     MpParams q = base;
     q.lay.ctas_per_sm = ctas;
     const int hq = heuristic_models_per_wave(q, models[0], n);
-    for (int mw : {hq, std::max(1, hq / 2), std::min(n, 2 * hq)}) {
+    const int64_t G = train_grid(q), tpm = q.tiles_per_model, T = q.total_tiles;
+    for (int64_t wt : {hq * tpm, std::max(1, hq / 2) * tpm, std::min(n, 2 * hq) * tpm, G, 2 * G, 4 * G, T}) {
+      wt = std::max<int64_t>(1, std::min(wt, T));
       bool dup = false;
-      for (const auto& c : cands) dup |= c.ctas_per_sm == ctas && c.models_per_wave == mw;
-      if (!dup) cands.push_back({ctas, mw});
+      for (const auto& c : cands) dup |= c.ctas_per_sm == ctas && c.wave_tiles == wt;
+      if (!dup) cands.push_back({ctas, wt});
     }
     if (ctas == 1) break;
   }
@@ -952,7 +950,7 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, Tun
   for (const auto& c : cands) {
     MpParams q = base;
     q.lay.ctas_per_sm = c.ctas_per_sm;
-    set_waves(q, n, c.models_per_wave);
+    set_wave_tiles(q, c.wave_tiles);
     if ((rc = launch_train(q, W, F, n, s)) != DVNR_OK) break;  // warm-up
     cudaEventRecord(e0, s);
     for (int r = 0; r < 3 && rc == DVNR_OK; ++r) rc = launch_train(q, W, F, n, s);
@@ -1074,12 +1072,12 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     }
     if (have) {
       p.lay.ctas_per_sm = ch.ctas_per_sm;
-      set_waves(p, n, ch.models_per_wave);
+      set_wave_tiles(p, ch.wave_tiles);
     } else {
       set_waves(p, m0, n);
     }
   }
-  if (c->exec && (c->models_per_wave != p.models_per_wave || c->ctas_per_sm != p.lay.ctas_per_sm ||
+  if (c->exec && (c->wave_tiles != p.wave_tiles || c->ctas_per_sm != p.lay.ctas_per_sm ||
                   c->scheduled != (p.sched != nullptr))) {
     DVNR_CUDA(cudaStreamSynchronize(s));
     cudaGraphExecDestroy(c->exec);
@@ -1087,7 +1085,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     c->exec = nullptr;
     c->graph = nullptr;
   }
-  c->models_per_wave = p.models_per_wave;
+  c->wave_tiles = p.wave_tiles;
   c->ctas_per_sm = p.lay.ctas_per_sm;
   c->scheduled = p.sched != nullptr;
   const int W = m0->mlp.width, F = m0->lv.F;
