@@ -860,7 +860,8 @@ int train_grid(const MpParams& p) {
 // and FP32 gradients into a quarter of the L2, but at least enough tiles
 // for half a tile per CTA; the autotuner also tries waves of whole grid
 // rounds (k tiles per CTA, which keep every CTA busy when models are small)
-// and a single wave. DVNR_WAVE_MODELS=v fixes waves of v models.
+// and a single wave. DVNR_WAVE_MODELS=v fixes waves of v models,
+// DVNR_WAVE_TILES=v waves of v tiles.
 int heuristic_models_per_wave(const MpParams& p, const dvnr_model m, int n_models) {
   int l2 = 0, dev = 0;
   cudaGetDevice(&dev);
@@ -883,7 +884,12 @@ void set_waves(MpParams& p, const dvnr_model m, int n_models) {
     const int v = atoi(e);
     if (v > 0) mw = v;
   }
-  set_wave_tiles(p, (int64_t)mw * p.tiles_per_model);
+  int64_t tiles = (int64_t)mw * p.tiles_per_model;
+  if (const char* e = getenv("DVNR_WAVE_TILES")) {  // waves of v tiles (may split models)
+    const long long v = atoll(e);
+    if (v > 0) tiles = v;
+  }
+  set_wave_tiles(p, tiles);
 }
 
 dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStream_t s) {
@@ -1049,7 +1055,8 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   p.models = c->d_models;
   {
     const char* at = getenv("DVNR_AUTOTUNE");
-    const bool tune = !(at && atoi(at) == 0) && !getenv("DVNR_WAVE_MODELS") && !profiling_on();
+    const bool tune = !(at && atoi(at) == 0) && !getenv("DVNR_WAVE_MODELS") && !getenv("DVNR_WAVE_TILES") &&
+                      !profiling_on();
     const std::string key = tune_key(m0, n, cfg);
     TuneChoice ch{0, 0};
     bool have = false;

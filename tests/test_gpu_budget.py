@@ -167,13 +167,17 @@ def test_fp16_model_that_stops_leaves_the_group(dv, orc):
     assert s1b["loss_ema"] == pytest.approx(s1b["last_loss"], rel=1e-6)
 
 
-def test_fp16_losses_cover_every_tile_after_a_model_leaves(dv, orc):
+@pytest.mark.parametrize("wave_tiles", [None, "5"])
+def test_fp16_losses_cover_every_tile_after_a_model_leaves(dv, orc, monkeypatch, wave_tiles):
     # weights frozen (lr 1e-30 moves no FP32 weight), so every step's loss is
     # the loss of the initial network on that step's samples. Model 1 stops
     # after its first step and leaves the middle of the group; from then on
     # models 0 and 2 are tiled over positions 0 and 1. Their losses at the
     # last step must equal the oracle's (mixed-precision forward) on the
     # same samples: a tile lost or counted twice moves the mean by 1/16.
+    # wave_tiles "5": waves of 5 tiles, which split every model's 16 tiles
+    if wave_tiles:
+        monkeypatch.setenv("DVNR_WAVE_TILES", wave_tiles)
     c = P.configs_blobs64()
     oc = P.oracle_cfg(c)
     FP16 = dv.A.DVNR_FP16

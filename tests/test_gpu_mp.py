@@ -170,7 +170,7 @@ def test_fp16_training_equal_psnr(dv, orc, A):
     assert abs(p16 - p32) < 0.2, (p16, p32)
 
 
-@pytest.mark.parametrize("wave_models", [None, "1", "3"])
+@pytest.mark.parametrize("wave_models", [None, "1", "3", "tiles:7"])
 def test_grouped_launch_models_are_independent(dv, A, monkeypatch, wave_models):
     # Four models in one grouped FP16 launch. Model 0 trained in the group
     # equals model 0 trained alone (same RNG slot) up to the reordering of
@@ -180,7 +180,10 @@ def test_grouped_launch_models_are_independent(dv, A, monkeypatch, wave_models):
 
     # wave_models: models trained per wave inside the launch (1: one model at
     # a time; 3: waves of 3 + 1); None leaves the library's choice (one wave)
-    if wave_models:
+    # ("tiles:7": waves of 7 tiles, which split the models' tile runs mid-model)
+    if wave_models and wave_models.startswith("tiles:"):
+        monkeypatch.setenv("DVNR_WAVE_TILES", wave_models[6:])
+    elif wave_models:
         monkeypatch.setenv("DVNR_WAVE_MODELS", wave_models)
     c = dict(P.configs_blobs64(), batch=2048)
     vols = [torch.from_numpy(volumes.blobs(32, seed=2000 + i)).cuda() for i in range(4)]
