@@ -26,7 +26,7 @@ constexpr int kTile = 128;
 #define DVNR_DEC_PAIR false
 #endif
 #ifndef DVNR_DEC_GROUP
-#define DVNR_DEC_GROUP 4
+#define DVNR_DEC_GROUP 2
 #endif
 #ifndef DVNR_TRAIN_PAIR
 #define DVNR_TRAIN_PAIR true
@@ -403,8 +403,17 @@ bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
   }
   lay.smem_act = off;
   lay.act_off[0] = 0;
-  for (int k = 1; k < H; ++k) lay.act_off[k] = (uint32_t)D + (uint32_t)(k - 1) * W;
-  off += ((uint32_t)D + (uint32_t)(H - 1) * W) * feat_bytes;
+  if (!train) {
+    // inference keeps only two activation tiles: H_k alternates between
+    // them (H_2 overwrites X0, whose layer has run), which lets one more CTA
+    // fit on an SM
+    const uint32_t R = (uint32_t)std::max(D, W);
+    for (int k = 1; k < H; ++k) lay.act_off[k] = (k & 1) ? R : 0u;
+    off += (H > 1 ? 2u * R : (uint32_t)D) * feat_bytes;
+  } else {
+    for (int k = 1; k < H; ++k) lay.act_off[k] = (uint32_t)D + (uint32_t)(k - 1) * W;
+    off += ((uint32_t)D + (uint32_t)(H - 1) * W) * feat_bytes;
+  }
   if (train) {
     // the weight-gradient product of dZ_H reads 128 features from its start
     const uint32_t need = lay.smem_dz + ((uint32_t)(H - 1) * W + 128) * feat_bytes;
@@ -428,14 +437,26 @@ bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
 }
 
 // CTAs of `kernel` resident per SM at `threads` threads and `smem` bytes of
-// dynamic shared memory (registers included), capped by `cap`: the grid of a
-// persistent launch is this times the SM count, one full wave.
+// dynamic shared memory, from the kernel's registers and shared memory
+// against the SM's register file and shared memory (1 KB reserved per CTA),
+// capped by `cap`: the grid of a persistent launch is this times the SM
+// count, one full wave. (The runtime's occupancy query answers 1 for these
+// kernels although 4 run side by side, so the limits are applied here.)
 template <class K>
 int resident_ctas(K kernel, int threads, size_t smem, int cap) {
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1)
-    n = 1;
-  return std::max(1, std::min(n, cap));
+  cudaFuncAttributes fa{};
+  int dev = 0, regs_sm = 65536, smem_sm = 228 * 1024;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * threads;
+  const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : cap;
+  const int by_smem = (int)((size_t)smem_sm / (smem + fa.sharedSizeBytes + 1024));
+  return std::max(1, std::min(std::min(by_regs, by_smem), cap));
 }
 
 }  // namespace

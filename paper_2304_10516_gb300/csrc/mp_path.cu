@@ -773,10 +773,18 @@ __global__ void __launch_bounds__(128) k_umma_selftest(int32_t* mismatches) {
 // ----------------------------------------------------------- host side -----
 template <int W, int F>
 void set_smem_attr(bool train, uint32_t bytes) {
-  if (train)
+  // the largest shared-memory carveout: these kernels hold big tiles in
+  // shared memory, and with no preference the occupancy query assumes a
+  // partition that fits one CTA per SM
+  if (train) {
     cudaFuncSetAttribute(k_mp_train<W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  else
+    cudaFuncSetAttribute(k_mp_train<W, F>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+  } else {
     cudaFuncSetAttribute(k_mp_decode<W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncSetAttribute(k_mp_decode<W, F>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+  }
 }
 
 template <int W, int F>
@@ -784,7 +792,11 @@ void launch_train_wf(const MpParams& p, int grid, cudaStream_t s) {
   k_mp_train<W, F><<<grid, kTile, p.lay.smem_bytes, s>>>(p);
 }
 template <int W, int F>
-void launch_decode_wf(const MpDecodeParams& p, int grid, cudaStream_t s) {
+void launch_decode_wf(const MpDecodeParams& p, cudaStream_t s) {
+  // one full wave of resident CTAs (registers can hold fewer per SM than
+  // shared and tensor memory allow)
+  const int per_sm = resident_ctas(k_mp_decode<W, F>, kTile, p.lay.smem_bytes, p.lay.ctas_per_sm);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p.n_tiles, (int64_t)sm_count() * per_sm));
   k_mp_decode<W, F><<<grid, kTile, p.lay.smem_bytes, s>>>(p);
 }
 
@@ -1226,10 +1238,9 @@ dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_m
   }
   const int W = m->mlp.width, F = m->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, false, lay.smem_bytes);
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(p.n_tiles, (int64_t)sm_count() * lay.ctas_per_sm));
   {
     ProfScope ps("decode_fp16", s);
-    DVNR_WF_DISPATCH(W, F, launch_decode_wf, p, grid, s);
+    DVNR_WF_DISPATCH(W, F, launch_decode_wf, p, s);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;
