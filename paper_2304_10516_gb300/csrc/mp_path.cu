@@ -8,9 +8,12 @@
 //   shared memory, FP32 accumulators in TMEM) -> L1/L2 loss with loss scale
 //   -> backward on tcgen05: dL/dH per layer, and the weight gradients of the
 //   whole run accumulated in TMEM -> dL/d(encoding) scattered into the FP32
-//   table gradients with vector atomics.
-// The fused Adam of util.cu follows; a step pair is replayed from a CUDA
-// graph. Decoding (Sec. 3, Sec. 4.1) runs the forward half on the same tiles.
+//   table gradients with vector atomics. When the run leaves a model, the
+//   CTA adds its accumulated weight gradients and loss to the model's.
+// The tiles of a step go in L2-sized waves; the fused Adam of util.cu
+// follows, and 32 steps are replayed from one CUDA graph. Decoding (Sec. 3,
+// Sec. 4.1) runs the forward half on the same tiles, at grid points, given
+// points or the samples of a ray lattice (direct rendering, Sec. 4.3).
 //
 // Tile buffers in shared memory hold 128 samples x features as FP16 core
 // matrices (8 samples x 8 features, 128 B): feature group g, sample group q
