@@ -145,3 +145,44 @@ def test_adaptive_encoding_matches_oracle(orc):
                 (n_vox, n_glob, lref, lmin, rref)
     with pytest.raises(A.DvnrError):
         dv.adaptive_encoding(10, 5)
+
+
+def test_null_arguments_rejected_by_newer_entry_points():
+    lib = A.load()
+    assert lib.dvnr_render_inr(None, 0, None, 1, 1, 1, None, None) == 1
+    assert lib.dvnr_render_in_frame(None, 0, None, None, None, 1, 1, 1, 0, None, None) == 1
+    assert lib.dvnr_composite(None, None, 0, 1, 1, None, None) == 1
+    assert lib.dvnr_freeze(None, None) == 1
+    assert lib.dvnr_export_fp16(None, None, 0) == 1
+    assert lib.dvnr_import_fp16(None, None, 0) == 1
+    h = C.c_void_p()
+    assert lib.dvnr_window_create(None, 1, None, None, 2, 0, C.byref(h)) == 1 and h.value is None
+    box = (A.dvnr_box * 1)(_box())
+    enc = (A.dvnr_enc_cfg * 1)(_enc())
+    mlp = A.dvnr_mlp_cfg(32, 2)
+    assert lib.dvnr_window_create(C.cast(box, C.c_void_p), 1, C.cast(enc, C.c_void_p), C.byref(mlp), 0, 0,
+                                  C.byref(h)) == 1  # capacity 0
+    assert lib.dvnr_window_push(None, None, None, None, None, None) == 1
+    assert lib.dvnr_window_range(None, None, None) == 1
+    assert lib.dvnr_window_model(None, 0, 0, None) == 1
+    assert lib.dvnr_window_bytes(None, None, None) == 1
+    lib.dvnr_window_destroy(None)  # ignored
+    assert lib.dvnr_adaptive_encoding(5, 10, 19, 12, 16.0, None) == 1
+
+
+@pytest.mark.parametrize("field,value", [("stop_decay", 1.0), ("stop_decay", -0.1), ("stop_loss", -1.0),
+                                         ("stop_loss", float("inf")), ("epochs", -1), ("min_steps", -3),
+                                         ("steps", -1), ("batch", 0)])
+def test_train_config_checked_on_host(field, value):
+    # the call fails on the configuration before it looks at any model
+    from paper_2304_10516_gb300 import model as dv
+
+    lib = A.load()
+    cfg = dv.TrainConfig()
+    setattr(cfg, field, value)
+    c = cfg.to_c()
+    hs = (C.c_void_p * 1)()
+    vs = (C.c_void_p * 1)()
+    rc = lib.dvnr_train(C.cast(hs, C.c_void_p), 1, C.cast(vs, C.c_void_p), C.byref(c), None, None)
+    assert rc == 1, (field, value)
+    assert lib.dvnr_last_error()
