@@ -51,6 +51,9 @@ CONFIGS = {
     # the 256^3 model's MLP and encoding width with a smaller table
     "w64d32h3": dict(L=16, F=2, log2T=14, base=16, growth=1.38, width=64, hidden=3, batch=4096),
     "w16d16h1_f4": dict(L=4, F=4, log2T=12, base=4, growth=1.5, width=16, hidden=1, batch=1000),
+    # one and eight features per level (the other widths of the grouped kernels)
+    "w32d16h2_f1": dict(L=16, F=1, log2T=13, base=4, growth=1.3, width=32, hidden=2, batch=2048),
+    "w32d32h2_f8": dict(L=4, F=8, log2T=12, base=6, growth=1.6, width=32, hidden=2, batch=1536),
 }
 
 
