@@ -427,7 +427,10 @@ dvnr_status dvnr_profile_enable(int32_t on);
 dvnr_status dvnr_profile_read(const char* kernel, double* total_ms, int64_t* launches);
 
 /* Number of kernels this library has launched since it was loaded; a CUDA
- * graph replay adds the kernel nodes it runs.                              */
+ * graph replay adds the kernel nodes it runs. The body runs of the
+ * early-stop training loop (a conditional graph node) are counted on the
+ * device: they are included once the stream that ran them has been
+ * synchronised.                                                            */
 int64_t dvnr_launch_count(void);
 
 /* Diagnostic of the tensor-core operand layouts used by the FP16 path: one

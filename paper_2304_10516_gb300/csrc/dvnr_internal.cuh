@@ -47,6 +47,11 @@ bool profiling_on();
 void count_launches(int64_t n);
 // Launches recorded into a CUDA graph are counted when the graph is replayed.
 void set_capturing(bool on);
+// A pinned host word, mapped into the device, that kernels add launch counts
+// to (included in dvnr_launch_count once the device has written it); freed
+// with its count kept. nullptr when pinned memory is not available.
+unsigned long long* device_counter_new();
+void device_counter_free(unsigned long long* p);
 
 // ----------------------------------------------------------- level table ----
 // Per-level layout of the hash-grid tables (kernel parameter, by value).

@@ -566,6 +566,30 @@ __global__ void __launch_bounds__(1024) k_mp_schedule(const MpModel* __restrict_
   if (tid == 0) sched[0] = base;
 }
 
+// Loop control of the early-stop training graph, which runs the steps of a
+// call as a conditional WHILE node whose body is a fixed number of steps
+// followed by this kernel. It sets the node's condition for the next body
+// run: some model of the group is still active (budget left, moving average
+// above the threshold) and fewer body runs than the call allows have been
+// made. arm >= 0 (the node in front of the loop) starts the run count at arm;
+// arm < 0 (the body's last node) continues it. Each granted run adds the
+// body's kernel count to the pinned host word `launches` (may be null).
+__global__ void __launch_bounds__(256) k_mp_continue(const MpModel* __restrict__ models, int n,
+                                                     int32_t* __restrict__ runs_left, int32_t arm,
+                                                     unsigned long long* launches, int32_t body_launches,
+                                                     cudaGraphConditionalHandle cond) {
+  int any = 0;
+  for (int m = threadIdx.x; m < n; m += blockDim.x) any |= model_active(models[m].st) ? 1 : 0;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    const int32_t r = arm >= 0 ? arm : *runs_left;
+    const bool go = any != 0 && r > 0;
+    *runs_left = go ? r - 1 : 0;
+    if (go && launches) *launches += (unsigned long long)body_launches;
+    cudaGraphSetConditional(cond, go ? 1u : 0u);
+  }
+}
+
 // --------------------------------------------------------- decode kernel ---
 template <int W, int F>
 __global__ void __launch_bounds__(kTile) k_mp_decode(const __grid_constant__ MpDecodeParams p) {
@@ -814,22 +838,45 @@ struct MpCache {
   int graph_steps = 0;
   MpModel* d_models = nullptr;
   AdamModelPtrs* d_adam = nullptr;
-  int32_t* d_sched = nullptr;  // active-model schedule, 1 + 2 n ints
+  int32_t* d_sched = nullptr;  // active-model schedule, 1 + 2 n ints, then the loop's run count
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
   int64_t wave_tiles = 0;
   int ctas_per_sm = 0;
   bool scheduled = false;  // the captured graph launches k_mp_schedule
-  void clear() {
+  // early-stop graph: arm node -> WHILE { steps, k_mp_continue }
+  bool looped = false;          // exec is that graph
+  bool loop_unavailable = false;  // building it failed once: fixed graphs only
+  cudaGraphNode_t arm_node = nullptr;
+  cudaKernelNodeParams arm_params{};
+  void* arm_args[7] = {};
+  const MpModel* arm_models = nullptr;
+  int arm_n = 0;
+  int32_t* arm_runs = nullptr;
+  int32_t arm_value = 0;
+  unsigned long long* arm_launches = nullptr;  // host word (device-mapped alias below)
+  unsigned long long* arm_launches_dev = nullptr;
+  int32_t arm_body = 0;
+  cudaGraphConditionalHandle arm_cond = 0;
+  void drop_graph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    arm_node = nullptr;
+    looped = false;
+    graph_steps = 0;
+  }
+  void clear() {
+    drop_graph();
+    device_counter_free(arm_launches);
+    arm_launches = nullptr;
+    arm_launches_dev = nullptr;
     if (d_models) cudaFree(d_models);
     if (d_adam) cudaFree(d_adam);
     if (d_sched) cudaFree(d_sched);
     if (cap) cudaStreamDestroy(cap);
-    exec = nullptr;
-    graph = nullptr;
     d_models = nullptr;
     d_adam = nullptr;
     d_sched = nullptr;
@@ -1002,6 +1049,75 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, Tun
   return DVNR_OK;
 }
 
+// The early-stop loop as one graph: an arm node (k_mp_continue with arm =
+// the call's bound on body runs, set before every launch) in front of a
+// conditional WHILE node whose body is G captured steps followed by
+// k_mp_continue. The loop ends when no model of the group is active, so a
+// group that stops early launches no further steps. DVNR_E_UNSUPPORTED when
+// the runtime refuses a conditional-node call or pinned memory for the
+// device-side launch count.
+template <class Step>
+dvnr_status build_loop_graph(MpCache* c, const MpModel* models, int n, int32_t* runs, int G, Step& one_step) {
+  const dvnr_status no = DVNR_E_UNSUPPORTED;
+  if (!c->arm_launches) {
+    c->arm_launches = device_counter_new();
+    c->arm_launches_dev = nullptr;
+    if (c->arm_launches && cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->arm_launches_dev),
+                                                    c->arm_launches, 0) != cudaSuccess)
+      c->arm_launches_dev = nullptr;
+  }
+  if (!c->arm_launches_dev) return no;
+  if (cudaGraphCreate(&c->graph, 0) != cudaSuccess) return no;
+  cudaGraphConditionalHandle cond = 0;
+  if (cudaGraphConditionalHandleCreate(&cond, c->graph, 0u, 0u) != cudaSuccess) return no;
+  c->arm_models = models;
+  c->arm_n = n;
+  c->arm_runs = runs;
+  c->arm_value = 0;
+  c->arm_body = 3 * G + 1;  // schedule, train, Adam per step, then k_mp_continue
+  c->arm_cond = cond;
+  void* args[7] = {&c->arm_models, &c->arm_n, &c->arm_runs, &c->arm_value, &c->arm_launches_dev,
+                   &c->arm_body, &c->arm_cond};
+  for (int i = 0; i < 7; ++i) c->arm_args[i] = args[i];
+  c->arm_params = cudaKernelNodeParams{};
+  c->arm_params.func = reinterpret_cast<void*>(k_mp_continue);
+  c->arm_params.gridDim = dim3(1, 1, 1);
+  c->arm_params.blockDim = dim3(256, 1, 1);
+  c->arm_params.sharedMemBytes = 0;
+  c->arm_params.kernelParams = c->arm_args;
+  c->arm_params.extra = nullptr;
+  cudaGraphNode_t arm = nullptr, loop = nullptr;
+  if (cudaGraphAddKernelNode(&arm, c->graph, nullptr, 0, &c->arm_params) != cudaSuccess) return no;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  if (cudaGraphAddNode(&loop, c->graph, &arm, nullptr, 1, &np) != cudaSuccess) return no;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  set_capturing(true);
+  cudaError_t e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  dvnr_status rc = DVNR_OK;
+  if (e == cudaSuccess) {
+    for (int k = 0; k < G && rc == DVNR_OK; ++k) rc = one_step(c->cap);
+    if (rc == DVNR_OK) {
+      k_mp_continue<<<1, 256, 0, c->cap>>>(models, n, runs, -1, c->arm_launches_dev, c->arm_body, cond);
+      e = cudaGetLastError();
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  set_capturing(false);
+  if (rc != DVNR_OK) return rc;
+  if (e != cudaSuccess) return no;
+  if (cudaGraphInstantiate(&c->exec, c->graph, 0) != cudaSuccess) return no;
+  c->arm_node = arm;
+  c->graph_steps = G;
+  c->looped = true;
+  return DVNR_OK;
+}
+
 }  // namespace
 
 bool mp_supported(const dvnr_model m) {
@@ -1049,7 +1165,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     }
     DVNR_CUDA(cudaMalloc(&c->d_models, sizeof(MpModel) * n));
     DVNR_CUDA(cudaMalloc(&c->d_adam, sizeof(AdamModelPtrs) * n));
-    DVNR_CUDA(cudaMalloc(&c->d_sched, sizeof(int32_t) * (1 + 2 * (size_t)n)));
+    DVNR_CUDA(cudaMalloc(&c->d_sched, sizeof(int32_t) * (2 + 2 * (size_t)n)));
     DVNR_CUDA(cudaMemcpy(c->d_models, hm.data(), sizeof(MpModel) * n, cudaMemcpyHostToDevice));
     DVNR_CUDA(cudaMemcpy(c->d_adam, ha.data(), sizeof(AdamModelPtrs) * n, cudaMemcpyHostToDevice));
     c->models.assign(models, models + n);
@@ -1102,10 +1218,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   if (c->exec && (c->wave_tiles != p.wave_tiles || c->ctas_per_sm != p.lay.ctas_per_sm ||
                   c->scheduled != (p.sched != nullptr))) {
     DVNR_CUDA(cudaStreamSynchronize(s));
-    cudaGraphExecDestroy(c->exec);
-    cudaGraphDestroy(c->graph);
-    c->exec = nullptr;
-    c->graph = nullptr;
+    c->drop_graph();
   }
   c->wave_tiles = p.wave_tiles;
   c->ctas_per_sm = p.lay.ctas_per_sm;
@@ -1125,15 +1238,27 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     }
     return DVNR_OK;
   }
-  const int G = 32;  // steps per graph replay
-  if (!c->exec || c->graph_steps != G) {
-    if (c->exec) {
-      cudaGraphExecDestroy(c->exec);
-      cudaGraphDestroy(c->graph);
-      c->exec = nullptr;
-      c->graph = nullptr;
+  const int G = 32;  // steps per graph replay (per body run of the early-stop loop)
+  // models that can leave the group (budgets, stop rule) run under the
+  // early-stop loop, which ends when none is left; the others, or a driver
+  // without conditional nodes, replay a fixed graph of G steps
+  const bool want_loop = p.sched != nullptr && !c->loop_unavailable;
+  if (c->exec && (c->graph_steps != G || c->looped != want_loop)) {
+    DVNR_CUDA(cudaStreamSynchronize(s));
+    c->drop_graph();
+  }
+  if (!c->cap) DVNR_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  if (!c->exec && want_loop) {
+    dvnr_status rc = build_loop_graph(c, p.models, n, c->d_sched + 1 + 2 * (size_t)n, G, one_step);
+    if (rc != DVNR_OK) {
+      // conditional nodes unavailable: keep the fixed graph for this cache
+      c->drop_graph();
+      c->loop_unavailable = true;
+      cudaGetLastError();
+      if (rc != DVNR_E_UNSUPPORTED) return rc;
     }
-    if (!c->cap) DVNR_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  }
+  if (!c->exec) {
     set_capturing(true);
     cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     dvnr_status rc = DVNR_OK;
@@ -1147,6 +1272,17 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     DVNR_CUDA(e);
     DVNR_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
     c->graph_steps = G;
+    c->looped = false;
+  }
+  if (c->looped) {
+    // at most ceil(steps / G) body runs: every model's budget is at most
+    // `steps`, and the step slots past a model's budget or stop are no-ops
+    const int64_t runs = (left + G - 1) / G;
+    c->arm_value = (int32_t)std::min<int64_t>(runs, 0x7FFFFFFF);
+    DVNR_CUDA(cudaGraphExecKernelNodeSetParams(c->exec, c->arm_node, &c->arm_params));
+    DVNR_CUDA(cudaGraphLaunch(c->exec, s));
+    count_launches(1);  // the arm node; the body runs count themselves on the device
+    return DVNR_OK;
   }
   while (left >= G) {
     DVNR_CUDA(cudaGraphLaunch(c->exec, s));

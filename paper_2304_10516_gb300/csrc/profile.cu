@@ -21,7 +21,36 @@ std::vector<Record> g_records;
 std::atomic<bool> g_on{false};
 std::atomic<int64_t> g_launches{0};
 thread_local bool g_capturing = false;
+// pinned, device-mapped words into which kernels add the launches of graph
+// bodies whose run count only the device knows (conditional WHILE bodies)
+std::vector<unsigned long long*> g_dev_counters;
 }  // namespace
+
+unsigned long long* device_counter_new() {
+  unsigned long long* p = nullptr;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&p), sizeof(*p), cudaHostAllocMapped) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  *p = 0ull;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_dev_counters.push_back(p);
+  return p;
+}
+
+void device_counter_free(unsigned long long* p) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (size_t i = 0; i < g_dev_counters.size(); ++i)
+      if (g_dev_counters[i] == p) {
+        g_dev_counters.erase(g_dev_counters.begin() + (std::ptrdiff_t)i);
+        break;
+      }
+    g_launches.fetch_add((int64_t)*reinterpret_cast<volatile unsigned long long*>(p));
+  }
+  cudaFreeHost(p);
+}
 
 bool profiling_on() { return g_on.load(); }
 void count_launches(int64_t n) { g_launches.fetch_add(n); }
@@ -85,6 +114,11 @@ dvnr_status dvnr_profile_read(const char* kernel, double* total_ms, int64_t* lau
   return DVNR_OK;
 }
 
-int64_t dvnr_launch_count(void) { return g_launches.load(); }
+int64_t dvnr_launch_count(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int64_t n = g_launches.load();
+  for (unsigned long long* p : g_dev_counters) n += (int64_t)*reinterpret_cast<volatile unsigned long long*>(p);
+  return n;
+}
 
 }  // extern "C"

@@ -204,3 +204,40 @@ def test_fp16_losses_cover_every_tile_after_a_model_leaves(dv, orc, monkeypatch,
         r = orc.fwd_bwd(oc, th0[slot].astype(np.float64), coords, t, loss=0, mixed=True,
                         loss_scale=float(2 ** round(np.log2(B))), want_grads=False)
         assert abs(s[slot]["last_loss"] - r["loss"]) <= 2e-3 * r["loss"], (slot, s[slot], r["loss"])
+
+
+def test_fp16_group_that_stops_ends_the_loop(dv):
+    # every model learns a constant field and meets the threshold within a
+    # few steps of a 3000-step budget. The steps of a call with a stop rule
+    # run as a conditional loop of 32-step bodies that ends once no model is
+    # active, so the call launches a few bodies, not 3000 steps of kernels
+    # that find nothing to do; each model's counters stop where it stopped.
+    # A second call on the same group (same cached graph) re-arms the loop.
+    from paper_2304_10516_gb300 import _abi as A
+
+    c = P.configs_blobs64()
+    FP16 = dv.A.DVNR_FP16
+    models, vols = _setup(dv, c)
+    vols = [torch.full_like(v, 0.25) for v in vols]
+    cfg = dv.TrainConfig(batch=2048, steps=3000, lr=5e-4, precision=FP16, seed=7,
+                         stop_loss=2e-3, stop_decay=0.5)
+    lib = A.load()
+    dv.train(models, vols, dv.TrainConfig(batch=2048, steps=1, lr=5e-4, precision=FP16, seed=7,
+                                          stop_loss=2e-3, stop_decay=0.5))  # launch-shape tuning
+    for call in range(2):
+        torch.cuda.synchronize()
+        n0 = lib.dvnr_launch_count()
+        it0 = [m.state()["iter"] for m in models]
+        dv.train(models, vols, cfg)
+        torch.cuda.synchronize()
+        launched = lib.dvnr_launch_count() - n0
+        s = [m.state() for m in models]
+        ran = [st["iter"] - i0 for st, i0 in zip(s, it0)]
+        for st, r in zip(s, ran):
+            assert st["stopped"] == 1 and 1 <= r < 100 and st["loss_ema"] < 2e-3, (call, st)
+            assert st["adam_t"] == st["iter"] and st["budget_end"] == st["iter"] - r + 3000
+        bodies = (max(ran) + 31) // 32
+        # begin-call kernels, the arm node, then 97 kernels per 32-step body;
+        # the masked schedule would have launched 3 x 3000
+        assert launched <= 16 + 1 + bodies * 97, (call, launched, ran)
+        assert launched >= 1 + bodies * 97, (call, launched, ran)
