@@ -60,6 +60,8 @@ WORKLOADS = {
                     width=32, hidden=2, batch=4096, steps_full=200, lam=0.0, lr=1e-2),
 }
 
+LEGS = ("roofline", "decode", "render", "render_inr", "e2e", "gain", "cpu")
+
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -75,6 +77,9 @@ def parse():
     p.add_argument("--precision", default="auto", choices=["auto", "fp16", "fp32"])
     p.add_argument("--no-extras", action="store_true",
                    help="skip the e2e, decode, render and CPU-baseline legs")
+    p.add_argument("--legs", default="all",
+                   help="spectral256: comma list of the extra legs to run, from " + ",".join(LEGS)
+                        + " (default all; e2e includes the FP32 path and PSNR, gain needs e2e)")
     return p.parse_args()
 
 
@@ -206,10 +211,66 @@ def run_ours(args, rank, world, local_rank):
     }
     if rank != 0:
         return None
-    if args.no_extras:
+    legs = set() if args.no_extras else (set(LEGS) if args.legs == "all" else set(args.legs.split(",")))
+    if legs - set(LEGS):
+        raise SystemExit(f"unknown legs {sorted(legs - set(LEGS))}; choose from {','.join(LEGS)}")
+    if not legs:
         return result
+    import ctypes as C
 
     # ---- dominant-kernel roofline: per-launch CUDA events on the launching stream
+    if "roofline" in legs:
+        result["roofline"] = roofline_leg(A, dv, model, vol, cfg, w, args)
+    # ---- decode and render of the trained model
+    torch.cuda.synchronize()
+    ex, ey, ez = nx, ny, nz
+    if legs & {"decode", "render", "render_inr"}:
+        out = torch.empty((ez, ey, ex), device=dev)
+        model.decode_grid(out)
+        torch.cuda.synchronize()
+    if "decode" in legs:
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        d0.record(stream)
+        for _ in range(reps):
+            model.decode_grid(out)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        dec_ms = d0.elapsed_time(d1) / reps
+        result["decode"] = {"value": ex * ey * ez / (dec_ms / 1e3), "unit": "decode samples/s",
+                            "ms": dec_ms, "points": ex * ey * ez}
+    if legs & {"render", "render_inr"}:
+        tf = dv.make_tf(alpha_max=0.05)
+        img = dv.render([model], tf, 1024, 1024, 512)
+        torch.cuda.synchronize()
+    if "render" in legs:
+        A.call("dvnr_profile_enable", 1)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        dv.render([model], tf, 1024, 1024, 512, out=img)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        tms, cnt = C.c_double(), C.c_int64()
+        A.call("dvnr_profile_read", b"render", C.byref(tms), C.byref(cnt))
+        A.call("dvnr_profile_enable", 0)
+        result["render"] = {"value": 1024 * 1024 * 512 / (tms.value / 1e3), "unit": "ray samples/s",
+                            "march_ms": tms.value, "decode_plus_march_ms": r0.elapsed_time(r1),
+                            "image": [1024, 1024], "samples_per_ray": 512}
+    # ---- the same frame marched through the network itself (no decoded grid)
+    if "render_inr" in legs:
+        result["render_inr"] = render_inr_leg(model, tf, img, out, stream)
+    if "e2e" in legs:
+        e2e_legs(result, dv, A, w, vol, vol_np, new_model, cfg, precision, gpu_index, rank,
+                 "gain" in legs)
+    # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
+    if "cpu" in legs:
+        result["cpu_baseline"] = cpu_baseline(w, vol_np)
+    return result
+
+
+def roofline_leg(A, dv, model, vol, cfg, w, args):
+    import ctypes as C
+
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -219,8 +280,6 @@ def run_ours(args, rank, world, local_rank):
     A.call("dvnr_profile_enable", 1)
     nprof = min(args.steps, 50)
     dv.train([model], [vol], cfg(nprof), sync=True)
-    import ctypes as C
-
     kern = {}
     names = ["train_fused_fp16", "mp_schedule", "adam", "minmax", "fp32_sample_encode",
              "fp32_gemm", "fp32_out_loss", "fp32_scatter"]
@@ -235,7 +294,7 @@ def run_ours(args, rank, world, local_rank):
     dms, dcnt = kern[dom]
     byt = kernel_bytes(dom, w, model.n_params, w["batch"])
     ach = byt / (dms / dcnt / 1e3) / 1e9 if byt else None
-    result["roofline"] = {
+    return {
         "kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
         "frac": (ach / hbm_peak) if ach else None, "traffic": measured_traffic(dom, args.workload),
         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
@@ -243,39 +302,9 @@ def run_ours(args, rank, world, local_rank):
         "share": {k: round(v[0] / total, 4) for k, v in kern.items()},
     }
 
-    # ---- decode and render of the trained model
-    torch.cuda.synchronize()
-    ex, ey, ez = nx, ny, nz
-    out = torch.empty((ez, ey, ex), device=dev)
-    model.decode_grid(out)
-    torch.cuda.synchronize()
-    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    d0.record(stream)
-    for _ in range(reps):
-        model.decode_grid(out)
-    d1.record(stream)
-    torch.cuda.synchronize()
-    dec_ms = d0.elapsed_time(d1) / reps
-    result["decode"] = {"value": ex * ey * ez / (dec_ms / 1e3), "unit": "decode samples/s",
-                        "ms": dec_ms, "points": ex * ey * ez}
-    tf = dv.make_tf(alpha_max=0.05)
-    img = dv.render([model], tf, 1024, 1024, 512)
-    torch.cuda.synchronize()
-    A.call("dvnr_profile_enable", 1)
-    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    r0.record(stream)
-    dv.render([model], tf, 1024, 1024, 512, out=img)
-    r1.record(stream)
-    torch.cuda.synchronize()
-    tms, cnt = C.c_double(), C.c_int64()
-    A.call("dvnr_profile_read", b"render", C.byref(tms), C.byref(cnt))
-    A.call("dvnr_profile_enable", 0)
-    result["render"] = {"value": 1024 * 1024 * 512 / (tms.value / 1e3), "unit": "ray samples/s",
-                        "march_ms": tms.value, "decode_plus_march_ms": r0.elapsed_time(r1),
-                        "image": [1024, 1024], "samples_per_ray": 512}
-    # ---- the same frame marched through the network itself (no decoded grid)
-    result["render_inr"] = render_inr_leg(model, tf, img, out, stream)
+
+def e2e_legs(result, dv, A, w, vol, vol_np, new_model, cfg, precision, gpu_index, rank, gain):
+    import torch
 
     # ---- end to end through the public API: host volume -> train -> loss
     pinned = torch.from_numpy(vol_np).pin_memory()
@@ -320,11 +349,8 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- what the learned network gains: against the untrained network and
     # against the raw-grid fallback (trilinear) at the model's FP16 byte size
-    result["learned_gain"] = learned_gain(trained.pop("model"), new_model(100 + rank), vol)
-
-    # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
-    result["cpu_baseline"] = cpu_baseline(w, vol_np)
-    return result
+    if gain:
+        result["learned_gain"] = learned_gain(trained.pop("model"), new_model(100 + rank), vol)
 
 
 def _profile(A, names):

@@ -314,6 +314,30 @@ __host__ __device__ __forceinline__ float frame_z(const RayFrame& f, int k) {
   return (f.lo[2] - 0.5f) + ((k + 0.5f) * (f.hi[2] - f.lo[2])) / (float)f.spr;
 }
 
+// Division of unsigned 64-bit integers by a divisor d >= 1 fixed for a
+// launch, by a multiply-high with the reciprocal m = floor((2^64 - 1) / d)
+// and a remainder correction (division by invariant integers, Granlund and
+// Montgomery 1994): num * m / 2^64 is below num / d by less than 2, so the
+// quotient estimate is q, q - 1 or q - 2 and at most two corrections make it
+// exact for every num < 2^64.
+struct FastDiv {
+  uint64_t d, m;
+};
+inline FastDiv make_fastdiv(uint64_t d) {
+  if (d == 0) d = 1;
+  return FastDiv{d, ~0ull / d};
+}
+__device__ __forceinline__ uint64_t fdiv(uint64_t num, const FastDiv& f) {
+  uint64_t q = __umul64hi(num, f.m);
+  uint64_t r = num - q * f.d;
+  if (r >= f.d) {
+    ++q;
+    r -= f.d;
+  }
+  if (r >= f.d) ++q;
+  return q;
+}
+
 __device__ __forceinline__ void value_range(const ModelState* st, float& vmin, float& inv_range) {
   vmin = ordered_to_float(st->enc_min);
   const float vmax = ordered_to_float(st->enc_max);

@@ -358,9 +358,11 @@ __device__ __forceinline__ uint32_t dec_unit_to_fixed(float g, float origin, int
   u = fminf(fmaxf(u, 0.f), 1.f);
   return (uint32_t)__float2uint_rn(u * 16777216.0f);
 }
-__device__ __forceinline__ uint32_t dec_grid_fixed(int64_t j, int64_t n) {
+// round(j / (n - 1) * 2^24) = floor((2^25 j + n - 1) / (2 (n - 1))); fd divides
+// by 2 (n - 1)
+__device__ __forceinline__ uint32_t dec_grid_fixed(uint64_t j, int64_t n, const FastDiv& fd) {
   if (n < 2) return 0u;
-  return (uint32_t)((2 * j * (int64_t)kFixOne + (n - 1)) / (2 * (n - 1)));
+  return (uint32_t)fdiv(2 * j * (uint64_t)kFixOne + (uint64_t)(n - 1), fd);
 }
 
 

@@ -103,6 +103,9 @@ struct MpDecodeParams {
   int32_t ghost;
   float origin[3];
   float* out;
+  // the launch's divisors: e[0], e[1] (grid point -> voxel), 2 (nstore[a] - 1)
+  // (voxel -> fixed point), nr and rb.npx (ray lattice)
+  FastDiv div_e0, div_e1, div_fix[3], div_nr, div_npx;
 };
 
 template <int F>
@@ -592,7 +595,7 @@ __global__ void __launch_bounds__(256) k_mp_continue(const MpModel* __restrict__
 
 // --------------------------------------------------------- decode kernel ---
 template <int W, int F>
-__global__ void __launch_bounds__(kTile) k_mp_decode(const __grid_constant__ MpDecodeParams p) {
+__global__ void __launch_bounds__(kTile, F <= 2 ? 4 : 1) k_mp_decode(const __grid_constant__ MpDecodeParams p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 8);
@@ -624,15 +627,18 @@ __global__ void __launch_bounds__(kTile) k_mp_decode(const __grid_constant__ MpD
     uint3 m = make_uint3(0u, 0u, 0u);
     if (valid) {
       if (p.grid_mode == 2) {
-        const int64_t k = i / p.nr, ray = p.r0 + (i - k * p.nr);
-        const int px = p.rb.px0 + (int)(ray % p.rb.npx), py = p.rb.py0 + (int)(ray / p.rb.npx);
+        const int64_t k = (int64_t)fdiv((uint64_t)i, p.div_nr), ray = p.r0 + (i - k * p.nr);
+        const int64_t ry = (int64_t)fdiv((uint64_t)ray, p.div_npx);
+        const int px = p.rb.px0 + (int)(ray - ry * p.rb.npx), py = p.rb.py0 + (int)ry;
         m = make_uint3(dec_unit_to_fixed(frame_x(p.rf, px), p.rb.origin[0], p.rb.nstore[0]),
                        dec_unit_to_fixed(frame_y(p.rf, py), p.rb.origin[1], p.rb.nstore[1]),
                        dec_unit_to_fixed(frame_z(p.rf, p.rb.k0 + (int)k), p.rb.origin[2], p.rb.nstore[2]));
       } else if (p.grid_mode) {
-        const int64_t x = i % p.e[0], y = (i / p.e[0]) % p.e[1], z = i / (p.e[0] * p.e[1]);
-        m = make_uint3(dec_grid_fixed(x + p.ghost, p.nstore[0]), dec_grid_fixed(y + p.ghost, p.nstore[1]),
-                       dec_grid_fixed(z + p.ghost, p.nstore[2]));
+        const uint64_t q1 = fdiv((uint64_t)i, p.div_e0), q2 = fdiv(q1, p.div_e1);
+        const uint64_t x = (uint64_t)i - q1 * (uint64_t)p.e[0], y = q1 - q2 * (uint64_t)p.e[1], z = q2;
+        m = make_uint3(dec_grid_fixed(x + p.ghost, p.nstore[0], p.div_fix[0]),
+                       dec_grid_fixed(y + p.ghost, p.nstore[1], p.div_fix[1]),
+                       dec_grid_fixed(z + p.ghost, p.nstore[2], p.div_fix[2]));
       } else {
         m = make_uint3(dec_unit_to_fixed(p.xyz[3 * i], p.origin[0], p.nstore[0]),
                        dec_unit_to_fixed(p.xyz[3 * i + 1], p.origin[1], p.nstore[1]),
@@ -1369,11 +1375,16 @@ dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_m
   }
   p.ghost = m->box.ghost;
   p.out = out;
+  p.div_e0 = make_fastdiv((uint64_t)p.e[0]);
+  p.div_e1 = make_fastdiv((uint64_t)p.e[1]);
+  for (int a = 0; a < 3; ++a) p.div_fix[a] = make_fastdiv(2 * (uint64_t)std::max<int64_t>(p.nstore[a] - 1, 1));
   if (rf) {
     p.rf = *rf;
     p.rb = *rb;
     p.r0 = r0;
     p.nr = nr;
+    p.div_nr = make_fastdiv((uint64_t)nr);
+    p.div_npx = make_fastdiv((uint64_t)rb->npx);
   }
   const int W = m->mlp.width, F = m->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, false, lay.smem_bytes);
