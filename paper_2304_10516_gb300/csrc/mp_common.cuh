@@ -31,6 +31,11 @@ constexpr int kTile = 128;
 #ifndef DVNR_TRAIN_PAIR
 #define DVNR_TRAIN_PAIR true
 #endif
+// CTAs per SM the decode kernel is built for (registers capped to fit)
+#ifndef DVNR_DEC_CTAS
+#define DVNR_DEC_CTAS 6
+#endif
+constexpr int kDecodeCtasPerSm = DVNR_DEC_CTAS;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s of SM clock per wait
 
 __device__ __forceinline__ uint32_t tile_off(uint32_t f, uint32_t s) {
@@ -406,12 +411,12 @@ bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
   lay.smem_act = off;
   lay.act_off[0] = 0;
   if (!train) {
-    // inference keeps only two activation tiles: H_k alternates between
-    // them (H_2 overwrites X0, whose layer has run), which lets one more CTA
-    // fit on an SM
-    const uint32_t R = (uint32_t)std::max(D, W);
-    for (int k = 1; k < H; ++k) lay.act_off[k] = (k & 1) ? R : 0u;
-    off += (H > 1 ? 2u * R : (uint32_t)D) * feat_bytes;
+    // inference keeps one activation tile: the epilogue of layer k writes
+    // H_(k+1) over the layer's input once its product has completed (the
+    // commit's mbarrier covers the operand reads), so that more CTAs fit on
+    // an SM
+    for (int k = 1; k < H; ++k) lay.act_off[k] = 0u;
+    off += (uint32_t)std::max(D, W) * feat_bytes;
   } else {
     for (int k = 1; k < H; ++k) lay.act_off[k] = (uint32_t)D + (uint32_t)(k - 1) * W;
     off += ((uint32_t)D + (uint32_t)(H - 1) * W) * feat_bytes;
@@ -434,7 +439,7 @@ bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
   if (lay.tmem_cols > 512 || lay.smem_bytes > 227 * 1024) return false;
   const int by_smem = (int)((228 * 1024) / (lay.smem_bytes + 1024));
   const int by_tmem = (int)(512 / lay.tmem_cols);
-  lay.ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_tmem), train ? 2 : 4));
+  lay.ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_tmem), train ? 2 : kDecodeCtasPerSm));
   return true;
 }
 

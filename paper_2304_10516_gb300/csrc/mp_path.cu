@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(256) k_mp_continue(const MpModel* __restrict__
 
 // --------------------------------------------------------- decode kernel ---
 template <int W, int F>
-__global__ void __launch_bounds__(kTile, F <= 2 ? 4 : 1) k_mp_decode(const __grid_constant__ MpDecodeParams p) {
+__global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_decode(const __grid_constant__ MpDecodeParams p) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 8);
@@ -649,7 +649,11 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? 4 : 1) k_mp_decode(const __gri
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
-    float h[W];
+    // the epilogues take the layer's W outputs in chunks of CH columns, so
+    // that few registers hold activations; the last one forms the output
+    // y = sum_j fp16(relu(h_j)) w_j in order j = 0 .. W-1
+    constexpr int CH = W >= 32 ? 32 : W;
+    float y = 0.f;
     for (int k = 0; k < H; ++k) {
       if (tid == 0) {
         umma::fence_after_sync();
@@ -661,41 +665,41 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? 4 : 1) k_mp_decode(const __gri
       __syncthreads();
       if (*abort_flag) goto teardown;
       umma::fence_after_sync();
+      const bool last = k == H - 1;
+      const uint32_t f0 = last ? 0u : p.lay.act_off[k + 1];
 #pragma unroll
-      for (int c = 0; c < W / 16; ++c) {
-        float v[16];
-        umma::ld16(tl + c * 16, v);
+      for (int c = 0; c < W / CH; ++c) {
+        float h[CH];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) h[c * 16 + j] = v[j];
-      }
-      umma::ld_wait();
-      if (k < H - 1) {
-        const uint32_t f0 = p.lay.act_off[k + 1];
+        for (int u = 0; u < CH / 16; ++u) {
+          float v[16];
+          umma::ld16(tl + c * CH + u * 16, v);
 #pragma unroll
-        for (int c = 0; c < W / 8; ++c) {
-          uint4 u;
-          uint32_t* pu = &u.x;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            __half2 q = __floats2half2_rn(fmaxf(h[c * 8 + 2 * j], 0.f), fmaxf(h[c * 8 + 2 * j + 1], 0.f));
-            pu[j] = *reinterpret_cast<uint32_t*>(&q);
-          }
-          *reinterpret_cast<uint4*>(s_act + tile_off(f0 + c * 8, tid)) = u;
+          for (int j = 0; j < 16; ++j) h[u * 16 + j] = v[j];
         }
-        umma::fence_proxy_async();
-      } else {
+        umma::ld_wait();
+        if (!last) {
 #pragma unroll
-        for (int j = 0; j < W; ++j) h[j] = __half2float(__float2half_rn(fmaxf(h[j], 0.f)));
+          for (int g = 0; g < CH / 8; ++g) {
+            uint4 u;
+            uint32_t* pu = &u.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              __half2 q = __floats2half2_rn(fmaxf(h[g * 8 + 2 * j], 0.f), fmaxf(h[g * 8 + 2 * j + 1], 0.f));
+              pu[j] = *reinterpret_cast<uint32_t*>(&q);
+            }
+            *reinterpret_cast<uint4*>(s_act + tile_off(f0 + c * CH + g * 8, tid)) = u;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < CH; ++j) y += __half2float(__float2half_rn(fmaxf(h[j], 0.f))) * s_wout[c * CH + j];
+        }
       }
+      if (!last) umma::fence_proxy_async();
       umma::fence_before_sync();
       __syncthreads();
     }
-    if (valid) {
-      float y = 0.f;
-#pragma unroll
-      for (int j = 0; j < W; ++j) y += h[j] * s_wout[j];
-      p.out[i] = y * range + vmin;
-    }
+    if (valid) p.out[i] = y * range + vmin;
   }
 teardown:
   if (*abort_flag && tid == 0) {
