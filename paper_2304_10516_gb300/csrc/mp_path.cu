@@ -11,9 +11,13 @@
 //   table gradients with vector atomics. When the run leaves a model, the
 //   CTA adds its accumulated weight gradients and loss to the model's.
 // The tiles of a step go in L2-sized waves; the fused Adam of util.cu
-// follows, and 32 steps are replayed from one CUDA graph. Decoding (Sec. 3,
-// Sec. 4.1) runs the forward half on the same tiles, at grid points, given
-// points or the samples of a ray lattice (direct rendering, Sec. 4.3).
+// follows, and 32 steps are replayed from one CUDA graph. A call whose models
+// can leave the group (per-model budgets, the moving-average stop) runs as
+// one graph launch whose conditional WHILE node repeats the 32 steps until
+// no model is active. Decoding (Sec. 3, Sec. 4.1) runs the forward half on
+// the same tiles, at grid points, given points or the samples of a ray
+// lattice (direct rendering, Sec. 4.3), with one ACT tile that each layer's
+// outputs overwrite.
 //
 // Tile buffers in shared memory hold 128 samples x features as FP16 core
 // matrices (8 samples x 8 features, 128 B): feature group g, sample group q
