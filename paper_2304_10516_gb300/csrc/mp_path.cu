@@ -883,6 +883,9 @@ struct MpCache {
     graph_steps = 0;
   }
   void clear() {
+    // a graph of an earlier call may still run on another stream, writing
+    // the launch counter and reading the descriptor tables
+    if (exec || arm_launches || d_models) cudaDeviceSynchronize();
     drop_graph();
     device_counter_free(arm_launches);
     arm_launches = nullptr;
