@@ -258,9 +258,15 @@ dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out);
  * tables, and one Adam step. vol_dev[i] is model i's stored block
  * ((hi-lo+2 ghost) voxels per axis). The value range is taken from the
  * volume first (min/max over all stored voxels).
- * FP16 precision: all n models run in one grouped kernel per step (they
- * must share one encoding and MLP configuration), the steps are replayed
- * from a CUDA graph. The first FP16 call for a configuration (encoding, MLP,
+ * FP16 precision: the models that share an encoding and MLP configuration
+ * run in one grouped kernel per step (one such launch per configuration
+ * present in the call), the steps are replayed from a CUDA graph. When the
+ * models' budgets differ or cfg->stop_loss is set, a call's steps run as a
+ * conditional WHILE graph node that ends once no model is active (the
+ * budget and stop tests run on the device; the host reads nothing during
+ * the call); a runtime that refuses conditional nodes, or the environment
+ * variable DVNR_GRAPH_LOOP=0, gets a fixed graph whose steps do nothing for
+ * models that left. The first FP16 call for a configuration (encoding, MLP,
  * batch, number of models) times a few launch shapes of the training kernel
  * on its models and volumes and keeps the fastest for the process; that call
  * synchronises the stream once (parameters, moments and step counters are

@@ -1258,8 +1258,11 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   const int G = 32;  // steps per graph replay (per body run of the early-stop loop)
   // models that can leave the group (budgets, stop rule) run under the
   // early-stop loop, which ends when none is left; the others, or a driver
-  // without conditional nodes, replay a fixed graph of G steps
-  const bool want_loop = p.sched != nullptr && !c->loop_unavailable;
+  // without conditional nodes, replay a fixed graph of G steps (whose steps
+  // do nothing for models that left). DVNR_GRAPH_LOOP=0 selects the fixed
+  // graph for every call.
+  const char* gl = getenv("DVNR_GRAPH_LOOP");
+  const bool want_loop = p.sched != nullptr && !c->loop_unavailable && !(gl && atoi(gl) == 0);
   if (c->exec && (c->graph_steps != G || c->looped != want_loop)) {
     DVNR_CUDA(cudaStreamSynchronize(s));
     c->drop_graph();

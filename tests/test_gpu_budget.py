@@ -206,14 +206,21 @@ def test_fp16_losses_cover_every_tile_after_a_model_leaves(dv, orc, monkeypatch,
         assert abs(s[slot]["last_loss"] - r["loss"]) <= 2e-3 * r["loss"], (slot, s[slot], r["loss"])
 
 
-def test_fp16_group_that_stops_ends_the_loop(dv):
+@pytest.mark.parametrize("loop", [True, False])
+def test_fp16_group_that_stops_ends_the_loop(dv, monkeypatch, loop):
     # every model learns a constant field and meets the threshold within a
     # few steps of a 3000-step budget. The steps of a call with a stop rule
     # run as a conditional loop of 32-step bodies that ends once no model is
     # active, so the call launches a few bodies, not 3000 steps of kernels
     # that find nothing to do; each model's counters stop where it stopped.
     # A second call on the same group (same cached graph) re-arms the loop.
+    # loop=False: the fallback for runtimes without conditional nodes, a
+    # fixed 32-step graph whose steps do nothing once every model stopped:
+    # the same per-model counters, and 3 kernels for every step slot.
     from paper_2304_10516_gb300 import _abi as A
+
+    if not loop:
+        monkeypatch.setenv("DVNR_GRAPH_LOOP", "0")
 
     c = P.configs_blobs64()
     FP16 = dv.A.DVNR_FP16
@@ -236,8 +243,11 @@ def test_fp16_group_that_stops_ends_the_loop(dv):
         for st, r in zip(s, ran):
             assert st["stopped"] == 1 and 1 <= r < 100 and st["loss_ema"] < 2e-3, (call, st)
             assert st["adam_t"] == st["iter"] and st["budget_end"] == st["iter"] - r + 3000
-        bodies = (max(ran) + 31) // 32
-        # begin-call kernels, the arm node, then 97 kernels per 32-step body;
-        # the masked schedule would have launched 3 x 3000
-        assert launched <= 16 + 1 + bodies * 97, (call, launched, ran)
-        assert launched >= 1 + bodies * 97, (call, launched, ran)
+        if loop:
+            bodies = (max(ran) + 31) // 32
+            # begin-call kernels, the arm node, then 97 kernels per 32-step
+            # body; the masked schedule launches 3 x 3000
+            assert launched <= 16 + 1 + bodies * 97, (call, launched, ran)
+            assert launched >= 1 + bodies * 97, (call, launched, ran)
+        else:
+            assert 3 * 3000 <= launched <= 16 + 3 * 3000, (call, launched, ran)
