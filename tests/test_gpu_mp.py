@@ -120,8 +120,12 @@ def test_fp16_ragged_batch_and_tail(dv, orc, A):
     assert abs(out["loss"].item() - r["loss"]) < 2e-3 * max(r["loss"], 1e-3)
 
 
-def test_fp16_decode_matches_oracle(dv, orc, A):
-    c = CONFIGS["w64d32h3"]
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+def test_fp16_decode_matches_oracle(dv, orc, A, name):
+    # every width / features-per-level / depth of the decode kernel (W = 16
+    # reads its outputs as one 16-column chunk, H = 1 forms the output in the
+    # first layer's epilogue); 26 048 points = 203.5 tiles (ragged tail)
+    c = CONFIGS[name]
     oc = P.oracle_cfg(c)
     theta = P.random_theta(oc, 7, table_scale=0.3)
     lo, hi, g = (3, 5, 7), (40, 37, 29), 1
