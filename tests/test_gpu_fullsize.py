@@ -209,3 +209,35 @@ def test_fullsize_partitioned_workload_losses(setup):
         assert abs(st["last_loss"] - r["loss"]) <= 2e-3 * r["loss"], (i, st["last_loss"], r["loss"])
         # (an Adam step of lr 1e-30 moves only parameters within ~1e-28 of zero)
         np.testing.assert_allclose(models[i].get_weights(), th, rtol=1e-6, atol=1e-25)
+
+
+def test_decode_grid_beyond_2_32_points(setup):
+    # the largest case: 2048 x 2048 x 1025 owned voxels = 4 299 161 600
+    # points (> 2^32, a 17 GB output), so the point and tile indices and the
+    # divisions that map a point to its voxel and fixed-point coordinates run
+    # past 32 bits. Sampled voxels on both sides of 2^31 and 2^32, the last
+    # voxel and random ones, against the oracle at the voxel's fixed-point
+    # coordinates (the oracle's own grid mapping).
+    orc, dv, c, oc, vol, theta = setup
+    dims = (2048, 2048, 1025)
+    N = dims[0] * dims[1] * dims[2]
+    if torch.cuda.mem_get_info()[0] < N * 4 + (4 << 30):
+        pytest.skip("needs about 21 GB of free device memory")
+    m = dv.Model((0, 0, 0), dims, 0, dv.EncodingConfig(c["L"], c["F"], c["log2T"], c["base"], c["growth"]),
+                 dv.MLPConfig(c["width"], c["hidden"]), seed=0)
+    m.set_weights(theta)
+    m.set_precision(1)
+    out = torch.empty((dims[2], dims[1], dims[0]), device="cuda")
+    m.decode_grid(out)
+    rng = np.random.default_rng(11)
+    idx = np.array([0, 1, 2 ** 31 - 1, 2 ** 31, 2 ** 31 + 1, 2 ** 32 - 1, 2 ** 32, 2 ** 32 + 1, N - 1]
+                   + list(rng.integers(0, N, size=200)), dtype=np.int64)
+    got = out.view(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    del out
+    x, y, z = idx % dims[0], (idx // dims[0]) % dims[1], idx // (dims[0] * dims[1])
+    mm = np.stack([[orc.grid_coord(int(j), n) for j in a] for a, n in ((x, dims[0]), (y, dims[1]), (z, dims[2]))],
+                  1).astype(np.uint32)
+    want = orc.decode_unit(oc, theta.astype(np.float64), mm, 0.0, 1.0, mixed=True)
+    err = np.abs(got - want).max()
+    assert err <= 2e-3 * max(1.0, np.abs(want).max()), err
+    m.close()
