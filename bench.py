@@ -78,8 +78,9 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip the e2e, decode, render and CPU-baseline legs")
     p.add_argument("--legs", default="all",
-                   help="spectral256: comma list of the extra legs to run, from " + ",".join(LEGS)
-                        + " (default all; e2e includes the FP32 path and PSNR, gain needs e2e)")
+                   help="comma list of the extra legs to run, from " + ",".join(LEGS)
+                        + " (default all; e2e includes the FP32 path and PSNR, gain needs e2e); "
+                          "blocks64 takes all or roofline")
     return p.parse_args()
 
 
@@ -465,6 +466,8 @@ def run_blocks(args, rank, world, local_rank):
     kern = _profile(A, ["train_fused_fp16", "mp_schedule", "adam", "minmax"])
     A.call("dvnr_profile_enable", 0)
     res["roofline"] = _roofline(kern, w, models[0].n_params * n, n * w["batch"], hbm, have)
+    if args.legs == "roofline":  # the roofline leg alone (profiling)
+        return res
     # full training from fresh models, then decode and PSNR over owned voxels
     for i, m in enumerate(models):
         m.close()
