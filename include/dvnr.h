@@ -84,7 +84,9 @@ typedef struct {
 /* ReLU MLP (Sec. 3; appendix: n_neurons, n_hidden_layers). n_hidden hidden
  * layers of `width` units, then one linear output. No biases.
  * Supported: width in {16, 32, 64}, 1 <= n_hidden <= 8. The FP16 path also
- * needs n_levels * n_features a multiple of 16 and at most 64.             */
+ * needs n_levels * n_features at most 64 and n_features in {1, 2, 4, 8}; an
+ * encoding width that is not a multiple of 16 (the appendix's 5 levels x 4
+ * features, for one) enters the first layer padded with zero features.     */
 typedef struct {
   int32_t width, n_hidden;
 } dvnr_mlp_cfg;

@@ -339,7 +339,7 @@ void dvnr_destroy(dvnr_model m) {
 dvnr_status dvnr_freeze(dvnr_model m, void* stream) {
   if (!m) return fail(DVNR_E_INVALID, "model is NULL");
   if (m->frozen) return DVNR_OK;
-  if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+  if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
   DVNR_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -533,7 +533,7 @@ dvnr_status dvnr_set_precision(dvnr_model m, int32_t precision, void* stream) {
   if (rc != DVNR_OK) return rc;
   if (m->frozen && precision != DVNR_FP16) return fail(DVNR_E_STATE, "a frozen model decodes in FP16 only");
   if (precision == DVNR_FP16 && m->precision != DVNR_FP16) {
-    if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+    if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
     if ((rc = launch_refresh_half(m, (cudaStream_t)stream)) != DVNR_OK) return rc;
   }
   m->precision = precision;
@@ -584,7 +584,7 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
   if (mixed) {
     for (int i = 0; i < n; ++i)
       if (!mp_supported(models[i]))
-        return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+        return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
   }
   std::vector<int64_t> budget((size_t)n);
   int64_t max_budget = 0;
@@ -683,7 +683,7 @@ dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev, const dvnr_train
   if (iteration < 0) return fail(DVNR_E_INVALID, "iteration must be >= 0");
   const bool mixed = cfg->precision == DVNR_FP16;
   if (mixed && !mp_supported(m))
-    return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+    return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
   if ((rc = use_device(m)) != DVNR_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   dvnr_step_outputs o{};
@@ -807,7 +807,7 @@ static dvnr_status check_inr(const dvnr_model* models, int32_t n) {
     if (models[i]->precision != models[0]->precision)
       return fail(DVNR_E_INVALID, "model %d: all models must use one precision", i);
     if (models[0]->precision == DVNR_FP16 && !mp_supported(models[i]))
-      return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features in {16,32,48,64}");
+      return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
   }
   return DVNR_OK;
 }

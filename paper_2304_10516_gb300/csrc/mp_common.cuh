@@ -48,6 +48,7 @@ __device__ __forceinline__ uint32_t wsm_off(uint32_t o, uint32_t i, uint32_t out
 
 struct MpLayout {
   uint32_t smem_wout, smem_w, smem_dz, smem_act, smem_bytes;
+  uint32_t dpad;  // encoding width rounded up to 16 (the K of layer 0; features D..dpad-1 are 0)
   uint32_t wbyte[kMaxHidden + 1];   // byte offset of W_k inside the weight area
   uint32_t act_off[kMaxHidden];     // feature offset of H_k in ACT (H_0 = X0)
   uint32_t tmem_cols;
@@ -143,9 +144,20 @@ __device__ __forceinline__ void st_row(uint8_t* base, uint32_t off, const float*
 // the grid in x order, where neighbouring lanes already share lines).
 constexpr int kLevelGroup = 4;
 
-template <int F, bool PAIR = true, int LG = kLevelGroup>
+// Features D .. dpad-1 of a sample's row (the zero padding of an encoding
+// whose width D is not a multiple of 16 up to layer 0's K): F at a time.
+template <int F>
+__device__ __forceinline__ void zero_pad_rows(int D, int dpad, uint8_t* act, uint32_t s) {
+  float z[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) z[f] = 0.f;
+  for (int f = D; f < dpad; f += F) st_row<F>(act, tile_off((uint32_t)f, s), z);
+}
+
+template <int F, bool PAIR = true, int LG = kLevelGroup, bool ZPAD = false>
 __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half* __restrict__ tab16,
-                                               uint3 m, bool valid, uint8_t* act, uint32_t s) {
+                                               uint3 m, bool valid, uint8_t* act, uint32_t s,
+                                               int dpad = 0) {
   for (int l0 = 0; l0 < lv.L; l0 += LG) {
     float v[LG][8][F];
     float fr[LG][3];
@@ -221,6 +233,7 @@ __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half*
       st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
     }
   }
+  if constexpr (ZPAD) zero_pad_rows<F>(lv.in_dim, dpad, act, s);
 }
 
 // Asynchronous copies global -> shared (cp.async, non-bulk): the issuing
@@ -323,6 +336,7 @@ __device__ __forceinline__ void encode_to_tile_staged(const LevelTab& lv, const 
 // with vector reductions. Returns true if a non-finite value was seen.
 // Load one model's FP16 weights into the core-matrix weight area and w_out
 // (as FP32) into s_wout.
+// W_0 takes lay.dpad input columns, those past D zero.
 __device__ void load_weights(const __half* __restrict__ theta16, const int64_t* w_off, int D, int H,
                              int W, const MpLayout& lay, uint8_t* smem) {
   uint8_t* s_w = smem + lay.smem_w;
@@ -334,6 +348,12 @@ __device__ void load_weights(const __half* __restrict__ theta16, const int64_t* 
     for (int e = threadIdx.x; e < W * in; e += blockDim.x) {
       const int o = e / in, i = e - o * in;
       *reinterpret_cast<__half*>(dst + wsm_off(o, i, W)) = src[e];
+    }
+    if (k == 0) {
+      for (int e = threadIdx.x; e < W * ((int)lay.dpad - D); e += blockDim.x) {
+        const int w = (int)lay.dpad - D, o = e / w, i = D + (e - o * w);
+        *reinterpret_cast<__half*>(dst + wsm_off(o, i, W)) = __float2half(0.f);
+      }
     }
   }
   for (int j = threadIdx.x; j < W; j += blockDim.x) s_wout[j] = __half2float(theta16[w_off[H] + j]);
@@ -389,8 +409,10 @@ uint32_t pow2_cols(uint32_t c) {
 }
 
 bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
-  const int W = m->mlp.width, H = m->mlp.n_hidden, D = m->lv.in_dim;
+  const int W = m->mlp.width, H = m->mlp.n_hidden;
+  const int D = (m->lv.in_dim + 15) / 16 * 16;  // layer 0's K: the encoding padded with zeros
   lay = MpLayout{};
+  lay.dpad = (uint32_t)D;
   uint32_t off = 64;  // mbarrier, TMEM slot, abort flag, spare
   lay.smem_wout = off;
   off += 64 * 4;

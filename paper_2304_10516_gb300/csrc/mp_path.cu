@@ -112,76 +112,94 @@ struct MpDecodeParams {
   FastDiv div_e0, div_e1, div_fix[3], div_nr, div_npx;
 };
 
+// One 16-column chunk of dL/d(encoding) (levels c/F .. c/F + 16/F - 1); with
+// GUARD, levels at or past L (the zero padding of the last chunk) are skipped.
+template <int F, bool GUARD>
+__device__ __forceinline__ bool scatter_chunk(const LevelTab& lv, float* __restrict__ grad, uint3 m,
+                                              const float (&d)[16], int c) {
+  bool bad = false;
+  constexpr int LPC = 16 / F;  // levels per 16-column chunk
+#pragma unroll
+  for (int q = 0; q < LPC; ++q) {
+    const int l = c / F + q;
+    if (GUARD && l >= lv.L) break;
+    uint32_t bx, by, bz;
+    float fx, fy, fz;
+    lattice(m.x, lv.N[l], bx, fx);
+    lattice(m.y, lv.N[l], by, fy);
+    lattice(m.z, lv.N[l], bz, fz);
+    float* tab = grad + lv.off[l];
+#pragma unroll
+    for (int f = 0; f < F; ++f) bad |= !isfinite(d[q * F + f]);
+    if constexpr (F <= 2) {
+      // x-neighbour corners whose entries form an aligned pair {2j, 2j+1}
+      // go out as one vector reduction of both entries
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t y = by + (r & 1), z = bz + (r >> 1);
+        const float wyz = ((r & 1) ? fy : 1.f - fy) * ((r >> 1) ? fz : 1.f - fz);
+        const float w0 = (1.f - fx) * wyz, w1 = fx * wyz;
+        const uint32_t i0 = corner_index(lv, l, bx, y, z);
+        const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
+        if (i1 == (i0 ^ 1u)) {
+          float g[2 * F];
+          const bool odd = (i0 & 1u) != 0u;
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            g[f] = (odd ? w1 : w0) * d[q * F + f];
+            g[F + f] = (odd ? w0 : w1) * d[q * F + f];
+          }
+          red_add<2 * F>(tab + (size_t)(i0 & ~1u) * F, g);
+        } else {
+          float g0[F], g1[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            g0[f] = w0 * d[q * F + f];
+            g1[f] = w1 * d[q * F + f];
+          }
+          red_add<F>(tab + (size_t)i0 * F, g0);
+          red_add<F>(tab + (size_t)i1 * F, g1);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
+                        (((k >> 2) & 1) ? fz : 1.f - fz);
+        const uint32_t idx =
+            corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+        float g[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) g[f] = w * d[q * F + f];
+        red_add<F>(tab + (size_t)idx * F, g);
+      }
+    }
+  }
+  return bad;
+}
+
 template <int F>
 __device__ __forceinline__ bool scatter_from_tmem(const LevelTab& lv, float* __restrict__ grad,
                                                   uint3 m, bool valid, uint32_t tl,
                                                   float* dbg_row, float inv_S) {
   bool bad = false;
-  constexpr int LPC = 16 / F;  // levels per 16-column chunk
-  for (int c = 0; c < lv.in_dim; c += 16) {
+  const int D = lv.in_dim;
+  int c = 0;
+  for (; c < D; c += 16) {
     float d[16];
     umma::ld16(tl + (uint32_t)c, d);
     umma::ld_wait();
     if (!valid) continue;
     if (dbg_row) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) dbg_row[c + j] = d[j] * inv_S;
+      for (int j = 0; j < 16; ++j)
+        if (c + j < D) dbg_row[c + j] = d[j] * inv_S;
     }
-#pragma unroll
-    for (int q = 0; q < LPC; ++q) {
-      const int l = c / F + q;
-      uint32_t bx, by, bz;
-      float fx, fy, fz;
-      lattice(m.x, lv.N[l], bx, fx);
-      lattice(m.y, lv.N[l], by, fy);
-      lattice(m.z, lv.N[l], bz, fz);
-      float* tab = grad + lv.off[l];
-#pragma unroll
-      for (int f = 0; f < F; ++f) bad |= !isfinite(d[q * F + f]);
-      if constexpr (F <= 2) {
-        // x-neighbour corners whose entries form an aligned pair {2j, 2j+1}
-        // go out as one vector reduction of both entries
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const uint32_t y = by + (r & 1), z = bz + (r >> 1);
-          const float wyz = ((r & 1) ? fy : 1.f - fy) * ((r >> 1) ? fz : 1.f - fz);
-          const float w0 = (1.f - fx) * wyz, w1 = fx * wyz;
-          const uint32_t i0 = corner_index(lv, l, bx, y, z);
-          const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
-          if (i1 == (i0 ^ 1u)) {
-            float g[2 * F];
-            const bool odd = (i0 & 1u) != 0u;
-#pragma unroll
-            for (int f = 0; f < F; ++f) {
-              g[f] = (odd ? w1 : w0) * d[q * F + f];
-              g[F + f] = (odd ? w0 : w1) * d[q * F + f];
-            }
-            red_add<2 * F>(tab + (size_t)(i0 & ~1u) * F, g);
-          } else {
-            float g0[F], g1[F];
-#pragma unroll
-            for (int f = 0; f < F; ++f) {
-              g0[f] = w0 * d[q * F + f];
-              g1[f] = w1 * d[q * F + f];
-            }
-            red_add<F>(tab + (size_t)i0 * F, g0);
-            red_add<F>(tab + (size_t)i1 * F, g1);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
-                          (((k >> 2) & 1) ? fz : 1.f - fz);
-          const uint32_t idx =
-              corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
-          float g[F];
-#pragma unroll
-          for (int f = 0; f < F; ++f) g[f] = w * d[q * F + f];
-          red_add<F>(tab + (size_t)idx * F, g);
-        }
-      }
-    }
+    // whole chunks of real levels, then a last chunk that ends in padding
+    if (c + 16 <= D)
+      bad |= scatter_chunk<F, false>(lv, grad, m, d, c);
+    else
+      bad |= scatter_chunk<F, true>(lv, grad, m, d, c);
   }
   return bad;
 }
@@ -211,6 +229,8 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) umma::tmem_alloc(tmem_slot, p.lay.tmem_cols);
+  // the zero padding of X0 (features D .. dpad-1): nothing else writes it
+  if ((int)p.lay.dpad > D) zero_pad_rows<F>(D, (int)p.lay.dpad, s_act, (uint32_t)tid);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -254,9 +274,23 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
           float v[16];
           umma::ld16(tl + p.lay.dw_col[k] + c, v);
           umma::ld_wait();
-          if (r < W) {
+          if (r < W && (in & 15) == 0) {
 #pragma unroll
             for (int j = 0; j < 4; ++j) red_add<4>(g + (size_t)r * in + c + 4 * j, v + 4 * j);
+          } else if (r < W) {
+            // columns past D (layer 0's zero padding) are dropped; a row of
+            // D % 4 != 0 inputs is not 16-byte aligned: scalar adds
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int c0 = c + 4 * j;
+              if (c0 + 4 <= in && (in & 3) == 0) {
+                red_add<4>(g + (size_t)r * in + c0, v + 4 * j);
+              } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  if (c0 + e < in) atomicAdd(g + (size_t)r * in + c0 + e, v[4 * j + e]);
+              }
+            }
           }
         }
       }
@@ -321,7 +355,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
       // all gathers of the tile in flight at once, staged in the dZ tile and
       // the hidden-activation tiles (idle until the forward pass)
       encode_to_tile_staged(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid, s_dz, H * W / 16,
-                            s_act + (uint32_t)D * 256u, (H - 1) * W / 16);
+                            s_act + p.lay.dpad * 256u, (H - 1) * W / 16);
     } else
 #endif
       encode_to_tile<F, DVNR_TRAIN_PAIR>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
@@ -336,7 +370,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     for (int k = 0; k < H; ++k) {
       if (tid == 0) {
         umma::fence_after_sync();
-        issue_forward(tmem, smem, p.lay, k, k == 0 ? D : W, W);
+        issue_forward(tmem, smem, p.lay, k, k == 0 ? (int)p.lay.dpad : W, W);
         umma::commit(mbar);
       }
       if (!mma_wait()) goto teardown;
@@ -450,7 +484,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     // -- backward: layer k maps H_{k-1} -> Z_k with W_{k-1}
     {
       for (int k = H; k >= 1; --k) {
-        const int in = k == 1 ? D : W;
+        const int in = k == 1 ? (int)p.lay.dpad : W;  // layer 0's K includes the zero padding
         if (tid == 0) {
           umma::fence_after_sync();
           const uint32_t dz0 = umma::smem_u32(s_dz) + ((uint32_t)((k - 1) * W) >> 3) * 2048u;
@@ -649,7 +683,8 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
                        dec_unit_to_fixed(p.xyz[3 * i + 2], p.origin[2], p.nstore[2]));
       }
     }
-    encode_to_tile<F, DVNR_DEC_PAIR, DVNR_DEC_GROUP>(p.lv, p.theta16, m, valid, s_act, (uint32_t)tid);
+    encode_to_tile<F, DVNR_DEC_PAIR, DVNR_DEC_GROUP, true>(p.lv, p.theta16, m, valid, s_act, (uint32_t)tid,
+                                                           (int)p.lay.dpad);
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
@@ -661,7 +696,7 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
     for (int k = 0; k < H; ++k) {
       if (tid == 0) {
         umma::fence_after_sync();
-        issue_forward(tmem, smem, p.lay, k, k == 0 ? D : W, W);
+        issue_forward(tmem, smem, p.lay, k, k == 0 ? (int)p.lay.dpad : W, W);
         umma::commit(mbar);
       }
       umma::mbar_wait_bounded(mbar, phase, abort_flag, kWaitCycles);
@@ -1141,7 +1176,7 @@ bool mp_supported(const dvnr_model m) {
   const int D = m->lv.in_dim, W = m->mlp.width, F = m->lv.F;
   if (!(W == 16 || W == 32 || W == 64)) return false;
   if (!(F == 1 || F == 2 || F == 4 || F == 8)) return false;
-  if (D % 16 != 0 || D < 16 || D > 64) return false;
+  if (D < 1 || D > 64) return false;  // padded with zeros to a multiple of 16 for layer 0
   MpLayout lay;
   return make_layout(m, true, lay) && make_layout(m, false, lay);
 }

@@ -54,6 +54,13 @@ CONFIGS = {
     # one and eight features per level (the other widths of the grouped kernels)
     "w32d16h2_f1": dict(L=16, F=1, log2T=13, base=4, growth=1.3, width=32, hidden=2, batch=2048),
     "w32d32h2_f8": dict(L=4, F=8, log2T=12, base=6, growth=1.6, width=32, hidden=2, batch=1536),
+    # the appendix's NekRS and S3D networks (n_levels 5 and 4, 4 features per
+    # level, 16 neurons, base resolution cbrt(T), per-level scale 2): an
+    # encoding width of 20 enters layer 0 padded with zeros to 32
+    "nekrs_w16d20h3_f4": dict(L=5, F=4, log2T=12, base=16, growth=2.0, width=16, hidden=3, batch=2048),
+    "s3d_w16d16h2_f4": dict(L=4, F=4, log2T=11, base=12, growth=2.0, width=16, hidden=2, batch=1500),
+    # width 10: padded to 16, and its layer-0 gradient rows are not 16-byte aligned
+    "w32d10h2_f2": dict(L=5, F=2, log2T=12, base=8, growth=1.5, width=32, hidden=2, batch=1200),
 }
 
 

@@ -122,7 +122,9 @@ def test_render_inr_fp32_matches_oracle(dv, orc):
     dict(L=16, F=2, log2T=14, base=16, growth=1.38, width=64, hidden=3, batch=4096),
     # another instantiation of the decode kernel's ray-lattice mode
     dict(L=16, F=1, log2T=13, base=4, growth=1.3, width=32, hidden=2, batch=2048),
-], ids=["w64f2h3", "w32f1h2"])
+    # the appendix's NekRS network: encoding width 20, padded to 32
+    dict(L=5, F=4, log2T=12, base=16, growth=2.0, width=16, hidden=3, batch=2048),
+], ids=["w64f2h3", "w32f1h2", "nekrs_w16d20h3"])
 def test_render_inr_fp16_matches_oracle(dv, orc, c):
     _check(dv, orc, c, BOXES, 1, dv.A.DVNR_FP16, 23, 17, 300, seed=50, dv_tol=2e-3)
 
