@@ -251,3 +251,37 @@ def test_fp16_group_that_stops_ends_the_loop(dv, monkeypatch, loop):
             assert launched >= 1 + bodies * 97, (call, launched, ran)
         else:
             assert 3 * 3000 <= launched <= 16 + 3 * 3000, (call, launched, ran)
+
+
+def test_appendix_nekrs_network_trains_on_fp16_path(dv, orc):
+    # the appendix's in situ NekRS network (5 levels x 4 features, 16 neurons,
+    # 3 hidden layers, lrate 0.001, 4 epochs, target loss 0.0105) through the
+    # appendix-key mapper: the epoch budget is the oracle's N_train^max, the
+    # call trains on the FP16 path, and the moving-average stop ends it no
+    # later than the budget
+    import json
+    import os
+
+    from paper_2304_10516_gb300 import config as PC
+    from paper_2304_10516_gb300 import volumes
+
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "appendix_configs.json")))
+    pc = PC.PaperConfig.from_dict(gold["insitu"]["NekRS"])
+    vol = torch.from_numpy(volumes.blobs(64, seed=1001)).cuda()
+    m = dv.Model((0, 0, 0), (64, 64, 64), 0, pc.encoding(), pc.mlp(), seed=3)
+    B = 4096
+    cfg = pc.train(batch=B, precision=dv.A.DVNR_FP16, seed=2)
+    dv.train([m], [vol], dv.TrainConfig(batch=B, steps=1, lr=1e-30, precision=dv.A.DVNR_FP16))
+    sse0, _ = dv.error_stats(m.decode_grid(), vol)  # the untrained network (value range set)
+    it0 = m.state()["iter"]
+    dv.train([m], [vol], cfg)
+    st = m.state()
+    budget = orc.max_iterations(64 ** 3, B, epochs=4)
+    ran = st["iter"] - it0
+    assert st["budget_end"] == it0 + budget
+    assert 1 <= ran <= budget and st["adam_t"] + st["skipped"] == st["iter"]
+    assert (st["stopped"] == 1) == (ran < budget)
+    if st["stopped"]:
+        assert st["loss_ema"] < 0.0105
+    sse, _ = dv.error_stats(m.decode_grid(), vol)
+    assert sse < 0.25 * sse0, (sse, sse0)  # the network has learned the field
