@@ -50,7 +50,7 @@ namespace {
 #endif
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
-[[maybe_unused]] constexpr int kTrainKernelRevision = 9;
+[[maybe_unused]] constexpr int kTrainKernelRevision = 10;
 
 struct MpModel {
   const __half* theta16;
