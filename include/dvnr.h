@@ -252,6 +252,13 @@ dvnr_status dvnr_set_precision(dvnr_model m, int32_t precision, void* stream);
  * if the last training volume held NaN/Inf (state still filled in).        */
 dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out);
 
+/* Set the value range that decoding de-normalises with (Sec. 4.1: outputs
+ * are y (vmax - vmin) + vmin), as training sets it from its volume: for a
+ * model restored from stored weights. vmin <= vmax, both finite (stored as
+ * float32); else DVNR_E_INVALID. Allowed on frozen models. Ordered after the
+ * work already on `stream`; synchronises the stream.                       */
+dvnr_status dvnr_set_value_range(dvnr_model m, double vmin, double vmax, void* stream);
+
 /* Train n models for cfg->steps iterations each (Sec. 3.2): per step and
  * model, sample cfg->batch coordinates (uniform and boundary, Sec. 3.3),
  * look up targets by trilinear interpolation of the model's volume after

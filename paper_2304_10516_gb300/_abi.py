@@ -31,7 +31,7 @@ EXPORTS = [
     "dvnr_error_stats_noalloc", "dvnr_export_fp16", "dvnr_import_fp16", "dvnr_render_inr",
     "dvnr_adaptive_encoding", "dvnr_freeze", "dvnr_window_create", "dvnr_window_destroy",
     "dvnr_window_push", "dvnr_window_range", "dvnr_window_model", "dvnr_window_bytes",
-    "dvnr_render_in_frame", "dvnr_composite",
+    "dvnr_render_in_frame", "dvnr_composite", "dvnr_set_value_range",
 ]
 
 
@@ -95,6 +95,7 @@ _SIGS = {
     "dvnr_copy_weights": ([_P, _P, _P], C.c_int),
     "dvnr_set_precision": ([_P, C.c_int32, _P], C.c_int),
     "dvnr_get_state": ([_P, C.POINTER(dvnr_state_info)], C.c_int),
+    "dvnr_set_value_range": ([_P, C.c_double, C.c_double, _P], C.c_int),
     "dvnr_train": ([_P, C.c_int32, _P, C.POINTER(dvnr_train_cfg), _P, _P], C.c_int),
     "dvnr_train_grad": ([_P, _P, C.POINTER(dvnr_train_cfg), C.c_int64,
                          C.POINTER(dvnr_step_outputs), _P], C.c_int),

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <vector>
 
@@ -564,6 +565,23 @@ dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out) {
   out->frozen = m->frozen ? 1 : 0;
   if (st.timeouts) return fail(DVNR_E_TIMEOUT, "a bounded device wait gave up (%u)", st.timeouts);
   if (st.nonfinite) return fail(DVNR_E_NONFINITE_INPUT, "the last training volume held NaN/Inf");
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_set_value_range(dvnr_model m, double vmin, double vmax, void* stream) {
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (!std::isfinite(vmin) || !std::isfinite(vmax) || !(vmin <= vmax) ||
+      !std::isfinite((float)vmin) || !std::isfinite((float)vmax))
+    return fail(DVNR_E_INVALID, "value range needs finite vmin <= vmax");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  // enc_min and enc_max are adjacent words of the device state
+  const uint32_t enc[2] = {float_to_ordered((float)vmin), float_to_ordered((float)vmax)};
+  static_assert(offsetof(ModelState, enc_max) == offsetof(ModelState, enc_min) + sizeof(uint32_t),
+                "value range words must be adjacent");
+  cudaStream_t s = (cudaStream_t)stream;
+  DVNR_CUDA(cudaMemcpyAsync(&m->st->enc_min, enc, sizeof(enc), cudaMemcpyHostToDevice, s));
+  DVNR_CUDA(cudaStreamSynchronize(s));
   return DVNR_OK;
 }
 

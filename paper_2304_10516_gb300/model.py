@@ -128,6 +128,49 @@ class Model:
         """Keep only the FP16 parameters and value range (storage form)."""
         A.call("dvnr_freeze", self._h, _stream(stream))
 
+    def set_value_range(self, vmin: float, vmax: float, stream=None):
+        """The range decoding de-normalises with (set by training otherwise)."""
+        A.call("dvnr_set_value_range", self._h, float(vmin), float(vmax), _stream(stream))
+
+    def save(self, path, fp16: bool = False):
+        """Write a versioned model file: box, configuration, value range and
+        the parameters as float32 (resume exactly) or binary16 (the paper's
+        16-bit storage)."""
+        from . import storage
+
+        st = self.state()
+        header = {"box": {"lo": list(self.lo), "hi": list(self.hi), "ghost": self.ghost},
+                  "encoding": {"n_levels": self.enc.n_levels, "n_features": self.enc.n_features,
+                               "log2_T": self.enc.log2_T, "base_res": self.enc.base_res,
+                               "growth": float(self.enc.growth)},
+                  "mlp": {"width": self.mlp.width, "n_hidden": self.mlp.n_hidden},
+                  "value_range": [float(st["vmin"]), float(st["vmax"])],
+                  "payload": "fp16" if fp16 else "fp32", "n_enc": self.n_enc, "n_mlp": self.n_mlp}
+        storage.write_model_file(path, header,
+                                 self.export_fp16().view(np.uint16) if fp16 else self.get_weights())
+
+    @classmethod
+    def load(cls, path, seed: int = 0) -> "Model":
+        """A model from a file written by save(): weights (an fp16 file sets
+        the FP32 weights to the widened binary16 values) and value range; the
+        optimiser state starts fresh."""
+        from . import storage
+
+        h, params = storage.read_model_file(path)
+        b, e, mm = h["box"], h["encoding"], h["mlp"]
+        m = cls(b["lo"], b["hi"], b["ghost"],
+                EncodingConfig(e["n_levels"], e["n_features"], e["log2_T"], e["base_res"], e["growth"]),
+                MLPConfig(mm["width"], mm["n_hidden"]), seed=seed)
+        if (m.n_enc, m.n_mlp) != (int(h["n_enc"]), int(h["n_mlp"])):
+            m.close()
+            raise ValueError("model file parameter counts do not match its configuration")
+        if h["payload"] == "fp16":
+            m.import_fp16(params.view(np.float16))
+        else:
+            m.set_weights(params)
+        m.set_value_range(*h["value_range"])
+        return m
+
     def __del__(self):
         try:
             self.close()

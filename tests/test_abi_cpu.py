@@ -153,6 +153,7 @@ def test_null_arguments_rejected_by_newer_entry_points():
     assert lib.dvnr_render_in_frame(None, 0, None, None, None, 1, 1, 1, 0, None, None) == 1
     assert lib.dvnr_composite(None, None, 0, 1, 1, None, None) == 1
     assert lib.dvnr_freeze(None, None) == 1
+    assert lib.dvnr_set_value_range(None, 0.0, 1.0, None) == 1
     assert lib.dvnr_export_fp16(None, None, 0) == 1
     assert lib.dvnr_import_fp16(None, None, 0) == 1
     h = C.c_void_p()

@@ -286,3 +286,37 @@ def test_fp16_export_import_roundtrip(dv):
     b.import_fp16(w16)
     np.testing.assert_array_equal(b.get_weights(), w16.astype(np.float32))
     assert a.n_params * 2 == w16.nbytes  # the stored model size in bytes
+
+
+@pytest.mark.parametrize("fp16", [False, True], ids=["fp32_file", "fp16_file"])
+def test_model_file_round_trip(dv, tmp_path, fp16):
+    # a trained model saved and loaded decodes bit for bit as the original on
+    # the path whose parameters the file holds (FP32 master weights and value
+    # range; or the binary16 weights, which the FP16 path computes with), and
+    # a value range set by hand de-normalises exactly
+    from paper_2304_10516_gb300 import model as M
+    from paper_2304_10516_gb300 import volumes
+
+    c = P.configs_blobs64()
+    vol = torch.from_numpy(volumes.blobs(64, seed=1001) * 3.0 - 1.0).cuda()  # range [-1, 2]
+    m = _model(dv, c, seed=9)
+    prec = dv.A.DVNR_FP16 if fp16 else dv.A.DVNR_FP32
+    dv.train([m], [vol], dv.TrainConfig(batch=c["batch"], steps=40, lr=1e-2, seed=4, precision=prec))
+    f = tmp_path / "m.dvnr"
+    m.save(f, fp16=fp16)
+    m2 = M.Model.load(f)
+    m2.set_precision(prec)
+    a, b = m.decode_grid().cpu().numpy(), m2.decode_grid().cpu().numpy()
+    np.testing.assert_array_equal(a.view(np.uint32), b.view(np.uint32))
+    s1, s2 = m.state(), m2.state()
+    assert (s1["vmin"], s1["vmax"]) == (s2["vmin"], s2["vmax"])
+    # de-normalisation: out = y (vmax - vmin) + vmin with the set range
+    m2.set_value_range(0.0, 1.0)
+    y = m2.decode_grid().cpu().numpy()
+    m2.set_value_range(-3.0, 5.0)
+    z = m2.decode_grid().cpu().numpy()
+    np.testing.assert_allclose(z, y * 8.0 - 3.0, rtol=0, atol=1e-5 * max(1.0, np.abs(z).max()))
+    with pytest.raises(Exception):
+        m2.set_value_range(2.0, 1.0)
+    m.close()
+    m2.close()
