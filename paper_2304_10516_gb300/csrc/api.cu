@@ -206,6 +206,7 @@ const char* dvnr_last_error(void) { return g_err; }
 
 dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr_mlp_cfg* mlp,
                         uint64_t seed, dvnr_model* out) {
+  dvnr::ApiRange nvtx_("dvnr_create");
   g_err[0] = 0;
   if (!out) return fail(DVNR_E_INVALID, "out is NULL");
   *out = nullptr;
@@ -338,6 +339,7 @@ void dvnr_destroy(dvnr_model m) {
 }
 
 dvnr_status dvnr_freeze(dvnr_model m, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_freeze");
   if (!m) return fail(DVNR_E_INVALID, "model is NULL");
   if (m->frozen) return DVNR_OK;
   if (!mp_supported(m)) return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
@@ -587,6 +589,7 @@ dvnr_status dvnr_set_value_range(dvnr_model m, double vmin, double vmax, void* s
 
 dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_dev,
                        const dvnr_train_cfg* cfg, void* stream, float* final_loss_host) {
+  dvnr::ApiRange nvtx_("dvnr_train");
   g_err[0] = 0;
   if (n < 1 || !models || !vol_dev) return fail(DVNR_E_INVALID, "need n >= 1 models and volumes");
   dvnr_status rc = check_train_cfg(cfg);
@@ -693,6 +696,7 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n, const float* const* vol_de
 
 dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev, const dvnr_train_cfg* cfg,
                             int64_t iteration, const dvnr_step_outputs* out, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_train_grad");
   g_err[0] = 0;
   if (!m || !vol_dev) return fail(DVNR_E_INVALID, "NULL model or volume");
   if (m->frozen) return fail(DVNR_E_STATE, "the model is frozen");
@@ -735,6 +739,7 @@ dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev, const dvnr_train
 
 dvnr_status dvnr_decode_points(dvnr_model m, const float* xyz_dev, int64_t n, float* out_dev,
                                void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_decode_points");
   if (!m) return fail(DVNR_E_INVALID, "model is NULL");
   if (n < 0) return fail(DVNR_E_INVALID, "n must be >= 0");
   if (n == 0) return DVNR_OK;
@@ -746,6 +751,7 @@ dvnr_status dvnr_decode_points(dvnr_model m, const float* xyz_dev, int64_t n, fl
 }
 
 dvnr_status dvnr_decode_grid(dvnr_model m, float* out_dev, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_decode_grid");
   if (!m || !out_dev) return fail(DVNR_E_INVALID, "NULL argument");
   dvnr_status rc = use_device(m);
   if (rc != DVNR_OK) return rc;
@@ -832,6 +838,7 @@ static dvnr_status check_inr(const dvnr_model* models, int32_t n) {
 
 dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w, int32_t h,
                         int32_t spr, float* rgba_dev, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_render");
   g_err[0] = 0;
   dvnr_status rc = check_render(models, n, tf, w, h, spr, rgba_dev);
   if (rc != DVNR_OK) return rc;
@@ -843,6 +850,7 @@ dvnr_status dvnr_render(const dvnr_model* models, int32_t n, const dvnr_tf* tf, 
 dvnr_status dvnr_render_in_frame(const dvnr_model* models, int32_t n, const int64_t frame_lo[3],
                                  const int64_t frame_hi[3], const dvnr_tf* tf, int32_t w, int32_t h,
                                  int32_t spr, int32_t from_network, float* rgba_dev, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_render_in_frame");
   g_err[0] = 0;
   dvnr_status rc = check_render(models, n, tf, w, h, spr, rgba_dev);
   if (rc != DVNR_OK) return rc;
@@ -861,6 +869,7 @@ dvnr_status dvnr_render_in_frame(const dvnr_model* models, int32_t n, const int6
 
 dvnr_status dvnr_composite(const float* const* rgba_dev, const double* depth_host, int32_t n, int32_t w,
                            int32_t h, float* out_dev, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_composite");
   g_err[0] = 0;
   if (n < 1 || !rgba_dev || !depth_host || !out_dev) return fail(DVNR_E_INVALID, "NULL argument or n < 1");
   if (w < 1 || h < 1) return fail(DVNR_E_INVALID, "w, h must be >= 1");
@@ -874,6 +883,7 @@ dvnr_status dvnr_composite(const float* const* rgba_dev, const double* depth_hos
 
 dvnr_status dvnr_render_inr(const dvnr_model* models, int32_t n, const dvnr_tf* tf, int32_t w,
                             int32_t h, int32_t spr, float* rgba_dev, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_render_inr");
   g_err[0] = 0;
   dvnr_status rc = check_render(models, n, tf, w, h, spr, rgba_dev);
   if (rc != DVNR_OK) return rc;

@@ -8,6 +8,7 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <cstring>
@@ -45,6 +46,15 @@ struct ProfScope {
 };
 bool profiling_on();
 void count_launches(int64_t n);
+// An NVTX range named after a public call, open for the call's duration (a
+// host-side marker for profilers; without an attached tool it costs a
+// branch).
+struct ApiRange {
+  explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+  ApiRange(const ApiRange&) = delete;
+  ApiRange& operator=(const ApiRange&) = delete;
+};
 // Launches recorded into a CUDA graph are counted when the graph is replayed.
 void set_capturing(bool on);
 // A pinned host word, mapped into the device, that kernels add launch counts

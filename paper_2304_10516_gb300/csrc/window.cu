@@ -80,6 +80,7 @@ void dvnr_window_destroy(dvnr_window w) {
 
 dvnr_status dvnr_window_push(dvnr_window w, const float* const* vol_dev, const dvnr_train_cfg* cfg,
                              void* stream, float* final_loss_host, int64_t* t_out) {
+  dvnr::ApiRange nvtx_("dvnr_window_push");
   if (!w || !vol_dev || !cfg) {
     dvnr::set_error("NULL argument");
     return DVNR_E_INVALID;
