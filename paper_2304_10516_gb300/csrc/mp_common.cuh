@@ -470,7 +470,7 @@ bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
 // against the SM's register file and shared memory (1 KB reserved per CTA),
 // capped by `cap`: the grid of a persistent launch is this times the SM
 // count, one full wave. (The runtime's occupancy query answers 1 for these
-// kernels although 4 run side by side, so the limits are applied here.)
+// kernels although 6 run side by side, so the limits are applied here.)
 template <class K>
 int resident_ctas(K kernel, int threads, size_t smem, int cap) {
   cudaFuncAttributes fa{};
