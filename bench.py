@@ -128,8 +128,8 @@ class ClockSampler:
 
 # ------------------------------------------------- algorithmic bytes/flops ---
 def kernel_bytes(name, w, n_params, batch):
-    """Algorithmic bytes of one launch of kernel `name` (per-unit figures x
-    units per launch; the figures are derived in the design doc)."""
+    """Algorithmic bytes of one launch of kernel `name`: the kernel's bytes
+    per unit (a sample, a parameter) times the units one launch processes."""
     L, F, W, H = w["L"], w["F"], w["width"], w["hidden"]
     D = L * F
     if name == "adam":
