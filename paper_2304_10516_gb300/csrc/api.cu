@@ -4,6 +4,7 @@
 // FP32 path and of the grouped FP16 tensor-core path (CUDA-graph replay),
 // decoding and rendering. Every call returns a status and never aborts.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -49,6 +50,8 @@ dvnr_status fail(dvnr_status s, const char* fmt, ...) {
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+std::atomic<uint64_t> g_next_uid{1};
 
 // Half-normal quantile table in 24-bit fixed point (Sec. 3.3 boundary
 // samples): knot k < 4096 at p = k/4096, the last knot at p = 1 - 2^-24,
@@ -223,6 +226,7 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
   }
   dvnr_model m = new (std::nothrow) dvnr_model_s();
   if (!m) return fail(DVNR_E_OOM, "host allocation failed");
+  m->uid = g_next_uid.fetch_add(1);
   m->box = *box;
   m->enc = *enc;
   m->mlp = *mlp;

@@ -155,6 +155,9 @@ struct Fp32Workspace {
 
 struct dvnr_model_s {
   int device = 0;
+  // process-wide unique id, never reused: caches keyed on models compare ids,
+  // since a destroyed model's handle address can come back for a new model
+  uint64_t uid = 0;
   dvnr_box box{};
   dvnr_enc_cfg enc{};
   dvnr_mlp_cfg mlp{};

@@ -880,7 +880,7 @@ void launch_decode_wf(const MpDecodeParams& p, cudaStream_t s) {
 // Per-model cache of the FP16 path: device tables of the last grouped call
 // and its captured CUDA graph.
 struct MpCache {
-  std::vector<dvnr_model> models;
+  std::vector<uint64_t> uids;  // dvnr_model_s::uid of each model of the cached call
   std::vector<const float*> vols;
   std::vector<uint32_t> slots;
   dvnr_train_cfg cfg{};
@@ -933,7 +933,7 @@ struct MpCache {
     d_adam = nullptr;
     d_sched = nullptr;
     cap = nullptr;
-    models.clear();
+    uids.clear();
     vols.clear();
     slots.clear();
     graph_steps = 0;
@@ -1201,9 +1201,9 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   if (!m0->mp) m0->mp = new MpCache();
   MpCache* c = static_cast<MpCache*>(m0->mp);
-  bool hit = c->d_models && (int)c->models.size() == n && same_cfg(c->cfg, *cfg);
+  bool hit = c->d_models && (int)c->uids.size() == n && same_cfg(c->cfg, *cfg);
   for (int i = 0; hit && i < n; ++i)
-    hit = c->models[i] == models[i] && c->vols[i] == vols[i] && c->slots[i] == slots[i];
+    hit = c->uids[i] == models[i]->uid && c->vols[i] == vols[i] && c->slots[i] == slots[i];
   if (!hit) {
     if (c->d_models) DVNR_CUDA(cudaStreamSynchronize(s));
     c->clear();
@@ -1220,7 +1220,8 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     DVNR_CUDA(cudaMalloc(&c->d_sched, sizeof(int32_t) * (2 + 2 * (size_t)n)));
     DVNR_CUDA(cudaMemcpy(c->d_models, hm.data(), sizeof(MpModel) * n, cudaMemcpyHostToDevice));
     DVNR_CUDA(cudaMemcpy(c->d_adam, ha.data(), sizeof(AdamModelPtrs) * n, cudaMemcpyHostToDevice));
-    c->models.assign(models, models + n);
+    c->uids.resize((size_t)n);
+    for (int i = 0; i < n; ++i) c->uids[i] = models[i]->uid;
     c->vols.assign(vols, vols + n);
     c->slots.assign(slots, slots + n);
     c->cfg = *cfg;
