@@ -60,7 +60,7 @@ WORKLOADS = {
                     width=32, hidden=2, batch=4096, steps_full=200, lam=0.0, lr=1e-2),
 }
 
-LEGS = ("roofline", "decode", "render", "render_inr", "e2e", "gain", "cpu")
+LEGS = ("roofline", "decode", "render", "render_inr", "e2e", "gain", "cpu", "batched", "insitu")
 
 SMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -146,6 +146,14 @@ def kernel_bytes(name, w, n_params, batch):
 
 
 # ------------------------------------------------------------ our arm -------
+def graph_stats(A):
+    import ctypes as C
+
+    c, r, e = C.c_int64(), C.c_int64(), C.c_int64()
+    A.call("dvnr_graph_stats", C.byref(c), C.byref(r), C.byref(e))
+    return c.value, r.value, e.value
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -169,33 +177,38 @@ def run_ours(args, rank, world, local_rank):
     enc = dv.EncodingConfig(w["L"], w["F"], w["log2T"], w["base"], w["growth"])
     mlp = dv.MLPConfig(w["width"], w["hidden"])
 
-    def new_model(seed):
-        return dv.Model((0, 0, 0), (nx, ny, nz), 0, enc, mlp, seed=seed)
+    def new_model(seed, enc_=enc):
+        return dv.Model((0, 0, 0), (nx, ny, nz), 0, enc_, mlp, seed=seed)
 
-    def cfg(steps, prec_code=precision):
+    def cfg(steps, prec_code=precision, seed=7 + rank):
         return dv.TrainConfig(batch=w["batch"], steps=steps, lr=w["lr"], lambda_bnd=w["lam"],
-                              precision=prec_code, seed=7 + rank)
+                              precision=prec_code, seed=seed)
 
     model = new_model(100 + rank)
     stream = torch.cuda.current_stream()
     gpu_index = local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0
-    clocks = ClockSampler(gpu_index)
-    # warm-up (untimed)
+    # warm-up (untimed): W steps, then one call of the timed step count, which
+    # captures the step graphs that count replays (a capture never falls in
+    # the timed region)
     dv.train([model], [vol], cfg(max(args.warmup, 3)), sync=True)
+    dv.train([model], [vol], cfg(args.steps), sync=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.barrier()
     torch.cuda.synchronize()
+    clocks = ClockSampler(gpu_index)
     launches0 = lib.dvnr_launch_count()
+    g0 = graph_stats(A)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     dv.train([model], [vol], cfg(args.steps), stream=stream, sync=False)
     e1.record(stream)
     torch.cuda.synchronize()
+    g1 = graph_stats(A)
     launches = lib.dvnr_launch_count() - launches0
-    ms = shard.max_over_ranks(e0.elapsed_time(e1))  # the slowest rank's time
     clk = clocks.stop()
+    ms = shard.max_over_ranks(e0.elapsed_time(e1))  # the slowest rank's time
     samples = w["batch"] * args.steps * world
     value = samples / (ms / 1e3)
     result = {
@@ -207,8 +220,14 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded random-phase k^-5/3 spectral field)",
         "config": {"workload": w["desc"], "global_batch": w["batch"] * world,
                    "parallelism": f"{world} independent partition models (no exchange)",
-                   "precision": prec, "l2": "working set > L2 (no flush needed)"},
+                   "precision": prec, "l2": "working set > L2 (no flush needed)",
+                   "warmup_extra": f"one untimed call of {args.steps} steps after the warm-up "
+                                   "(captures the step graphs the timed call replays)"},
         "clocks": clk, "gpu_launches": int(launches),
+        "graph": {"captures_in_timed_region": g1[0] - g0[0], "graph_launches": g1[1] - g0[1],
+                  "eager_steps": g1[2] - g0[2],
+                  "layout": "graphs of 32, 16 and 8 steps for the binary digits of the step "
+                            "count; fewer than 8 remaining steps launched directly"},
     }
     if rank != 0:
         return None
@@ -260,12 +279,22 @@ def run_ours(args, rank, world, local_rank):
     # ---- the same frame marched through the network itself (no decoded grid)
     if "render_inr" in legs:
         result["render_inr"] = render_inr_leg(model, tf, img, out, stream)
+    model.close()
     if "e2e" in legs:
         e2e_legs(result, dv, A, w, vol, vol_np, new_model, cfg, precision, gpu_index, rank,
                  "gain" in legs)
     # ---- CPU baseline: the FP64 oracle on a bounded sample of the workload
     if "cpu" in legs:
         result["cpu_baseline"] = cpu_baseline(w, vol_np)
+    # ---- the other two workloads of the metric, measured in the same run:
+    # 64 uneven partitions in one grouped launch, and the in situ time series
+    if "batched" in legs and args.workload == "spectral256":
+        del vol
+        torch.cuda.empty_cache()
+        result["batched"] = blocks_measure(args, rank, world, local_rank, compact=True)
+    if "insitu" in legs and args.workload == "spectral256":
+        torch.cuda.empty_cache()
+        result["insitu"] = insitu_measure(args, rank, world, local_rank, compact=True)
     return result
 
 
@@ -295,63 +324,94 @@ def roofline_leg(A, dv, model, vol, cfg, w, args):
     dms, dcnt = kern[dom]
     byt = kernel_bytes(dom, w, model.n_params, w["batch"])
     ach = byt / (dms / dcnt / 1e3) / 1e9 if byt else None
+    traffic, src = measured_traffic(dom, args.workload)
     return {
         "kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-        "frac": (ach / hbm_peak) if ach else None, "traffic": measured_traffic(dom, args.workload),
+        "frac": (ach / hbm_peak) if ach else None, "traffic": traffic, "traffic_source": src,
         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-        "avg_launch_ms": dms / dcnt,
+        "avg_launch_ms": dms / dcnt, "algorithmic_bytes_per_launch": byt,
         "share": {k: round(v[0] / total, 4) for k, v in kern.items()},
     }
 
 
-def e2e_legs(result, dv, A, w, vol, vol_np, new_model, cfg, precision, gpu_index, rank, gain):
+def _mean_se(xs):
+    m = statistics.fmean(xs)
+    se = statistics.stdev(xs) / math.sqrt(len(xs)) if len(xs) > 1 else float("nan")
+    return m, se
+
+
+def e2e_legs(result, dv, A, w, vol, vol_np, new_model, cfg, precision, gpu_index, rank, gain,
+             seeds=4):
+    """End to end through the public API, then the "equal PSNR" statistic:
+    the production path and the plain FP32 path each trained from the same
+    `seeds` seeded initialisations and sample streams for the full step count;
+    mean PSNR difference with its standard error (paired by seed)."""
     import torch
 
-    # ---- end to end through the public API: host volume -> train -> loss
+    # ---- end to end: host volume -> device -> train -> loss to host
     pinned = torch.from_numpy(vol_np).pin_memory()
     dvol = torch.empty_like(vol)
+    steps_full = w["steps_full"]
 
-    trained = {}
-
-    def e2e(prec_code, reps):
-        m = new_model(100 + rank)
-        w0 = m.get_weights()
-        res = []
-        for r in range(reps):
-            if r:
-                m.set_weights(w0)  # same initial weights and fresh optimiser state
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            dvol.copy_(pinned, non_blocking=True)
-            loss = dv.train([m], [dvol], cfg(w["steps_full"], prec_code), sync=True)
-            t1 = time.perf_counter()
-            res.append(t1 - t0)
-        dec = m.decode_grid()
-        sse, mx = dv.error_stats(dec, vol)
-        mse = sse / vol.numel()
-        if prec_code == precision:
-            trained["model"] = m
-        else:
-            m.close()
-        return min(res), 10 * math.log10(1.0 / mse), mx, loss[0]
+    def psnr_of(m):
+        sse, mx = dv.error_stats(m.decode_grid(), vol)
+        return 10 * math.log10(1.0 / (sse / vol.numel())), mx
 
     clocks_e2e = ClockSampler(gpu_index)
-    t_mp, psnr_mp, mx_mp, loss_mp = e2e(precision, 2)
-    t_32, psnr_32, mx_32, loss_32 = e2e(A.DVNR_FP32, 1)
+    m = new_model(100 + rank)
+    w0 = m.get_weights()
+    t_e2e = []
+    for r in range(2):
+        if r:
+            m.set_weights(w0)  # same initial weights and fresh optimiser state
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dvol.copy_(pinned, non_blocking=True)
+        dv.train([m], [dvol], cfg(steps_full), sync=True)
+        t_e2e.append(time.perf_counter() - t0)
     result["clocks_e2e"] = clocks_e2e.stop()
-    steps_full = w["steps_full"]
-    result["e2e"] = {"value": steps_full * w["batch"] / t_mp, "unit": "train samples/s",
+    result["e2e"] = {"value": steps_full * w["batch"] / min(t_e2e), "unit": "train samples/s",
                      "h2d_bytes_per_step": int(vol.numel() * 4), "d2h_bytes_per_step": 4,
                      "step": f"upload volume, {steps_full} training iterations, read loss"}
-    result["psnr"] = {"path": psnr_mp, "fp32_path": psnr_32, "delta_db": psnr_mp - psnr_32,
-                      "max_abs": mx_mp, "fp32_max_abs": mx_32, "steps": steps_full}
-    result["fp32_path"] = {"value": steps_full * w["batch"] / t_32, "unit": "train samples/s",
+    m.close()
+    del dvol, pinned
+    # ---- equal PSNR: `seeds` paired runs of both paths on the resident volume
+    runs = []
+    t_mp = t_32 = 0.0
+    trained = None
+    for k in range(seeds):
+        row = {"init_seed": 100 + rank + k, "sample_seed": 7 + rank + k}
+        for name, code in (("path", precision), ("fp32_path", A.DVNR_FP32)):
+            m = new_model(row["init_seed"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dv.train([m], [vol], cfg(steps_full, code, seed=row["sample_seed"]), sync=True)
+            dt = time.perf_counter() - t0
+            if code == precision:
+                t_mp += dt
+            else:
+                t_32 += dt
+            row[name], row[name + "_max_abs"] = psnr_of(m)
+            if k == 0 and code == precision and gain:
+                trained = m
+            else:
+                m.close()
+        runs.append(row)
+    d = [r["path"] - r["fp32_path"] for r in runs]
+    dm, dse = _mean_se(d)
+    pm, pse = _mean_se([r["path"] for r in runs])
+    fm, fse = _mean_se([r["fp32_path"] for r in runs])
+    result["psnr"] = {"path_mean": pm, "path_se": pse, "fp32_path_mean": fm, "fp32_path_se": fse,
+                      "delta_db_mean": dm, "delta_db_se": dse, "equal_psnr": abs(dm) <= 0.2,
+                      "gate_db": 0.2, "runs": runs, "steps": steps_full, "seeds": seeds,
+                      "note": "delta = FP16 path - plain FP32 path, paired by seed; PSNR over "
+                              "all voxels from the FP64 error reduction"}
+    result["fp32_path"] = {"value": seeds * steps_full * w["batch"] / t_32, "unit": "train samples/s",
                            "speedup": t_32 / t_mp}
-
     # ---- what the learned network gains: against the untrained network and
     # against the raw-grid fallback (trilinear) at the model's FP16 byte size
     if gain:
-        result["learned_gain"] = learned_gain(trained.pop("model"), new_model(100 + rank), vol)
+        result["learned_gain"] = learned_gain(trained, new_model(100 + rank), vol, dv, w, new_model, cfg)
 
 
 def _profile(A, names):
@@ -380,21 +440,25 @@ def _roofline(kern, w, n_params, units, hbm_peak, have_peaks):
 
 
 def measured_traffic(kernel, workload):
-    """DRAM bytes per launch of the training kernel from the committed ncu
-    summary, if it was taken on the current kernel revision (else None)."""
+    """(DRAM bytes per launch, provenance) of the training kernel from the
+    committed ncu summary, if that summary was taken on the current kernel
+    revision (else None)."""
     import re
 
     if kernel != "train_fused_fp16" or workload != "spectral256":
-        return None
+        return None, None
+    path = os.path.join("profiles", "k_mp_train_fp16_spectral256.md")
     try:
         src = open(os.path.join(ROOT, "paper_2304_10516_gb300", "csrc", "mp_path.cu")).read()
         rev = int(re.search(r"kTrainKernelRevision = (\d+);", src).group(1))
-        prof = open(os.path.join(ROOT, "profiles", "k_mp_train_fp16_spectral256.md")).read()
+        prof = open(os.path.join(ROOT, path)).read()
         prev = int(re.search(r"kernel revision: (\d+)", prof).group(1))
         traffic = int(re.search(r"traffic_bytes_per_launch: (\d+)", prof).group(1))
     except Exception:
-        return None
-    return traffic if rev == prev else None
+        return None, None
+    if rev != prev:
+        return None, f"{path} was taken on kernel revision {prev}, the kernel is at {rev}"
+    return traffic, f"one ncu capture committed in {path} (kernel revision {rev}), not this run"
 
 
 def _peaks():
@@ -405,9 +469,15 @@ def _peaks():
         return 6800.0, False
 
 
-def run_blocks(args, rank, world, local_rank):
+def blocks_measure(args, rank, world, local_rank, compact=False):
     """The partitioned workload: 64 uneven blocks of a 1024x1024x512 field,
-    one INR each, all trained by one grouped launch per step."""
+    one INR each, all of a GPU's blocks trained by one grouped launch per
+    step. Under torchrun the ranks split the one global decomposition by
+    longest-processing-time on voxel count (Sec. 3.1: no exchange while
+    training), so the total work is fixed (strong scaling); the frame is
+    rendered per rank and composited sort-last, the PSNR reduced over ranks.
+    compact: the sub-object of the default run (throughput, roofline, PSNR
+    of the production path and of the plain FP32 path, decode)."""
     import torch
 
     from paper_2304_10516_gb300 import _abi as A
@@ -418,60 +488,78 @@ def run_blocks(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = WORKLOADS["blocks64"]
     lib = A.load()
-    field = volumes.spectral_torch(w["shape"], seed=w["seed"] + rank, device=dev)
-    boxes = volumes.uneven_boxes((512, 512, 512), (4, 4, 4), (96, 160), seed=w["seed"])
+    field = volumes.spectral_torch(w["shape"], seed=w["seed"], device=dev)
+    boxes_all = volumes.uneven_boxes((512, 512, 512), (4, 4, 4), (96, 160), seed=w["seed"])
+    costs = [int(np.prod([h - l + 2 for l, h in zip(lo, hi)])) for lo, hi in boxes_all]
+    mine = shard.rank_partitions(costs, world, rank)
+    boxes = [boxes_all[i] for i in mine]
     vols = [volumes.extract_block(field, lo, hi, 1) for lo, hi in boxes]
     enc = dv.EncodingConfig(w["L"], w["F"], w["log2T"], w["base"], w["growth"])
     mlp = dv.MLPConfig(w["width"], w["hidden"])
-    models = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
+
+    def fresh():
+        return [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in zip(mine, boxes)]
+
+    models = fresh()
     n = len(models)
 
     def cfg(steps, prec=A.DVNR_FP16):
         return dv.TrainConfig(batch=w["batch"], steps=steps, lr=w["lr"], lambda_bnd=w["lam"],
-                              sigma_bnd=0.005, precision=prec, seed=7 + rank)
+                              sigma_bnd=0.005, precision=prec, seed=7)
 
     stream = torch.cuda.current_stream()
-    clocks = ClockSampler(0 if "CUDA_VISIBLE_DEVICES" in os.environ else local_rank)
+    # warm-up, then one untimed call of the timed step count (step graphs)
     dv.train(models, vols, cfg(max(args.warmup, 3)))
+    dv.train(models, vols, cfg(args.steps))
     if world > 1:
         import torch.distributed as dist
 
         dist.barrier()
     torch.cuda.synchronize()
+    clocks = ClockSampler(0 if "CUDA_VISIBLE_DEVICES" in os.environ else local_rank)
     l0 = lib.dvnr_launch_count()
+    g0 = graph_stats(A)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     dv.train(models, vols, cfg(args.steps), sync=False)
     e1.record(stream)
     torch.cuda.synchronize()
+    g1 = graph_stats(A)
     ms = shard.max_over_ranks(e0.elapsed_time(e1))
     launches = lib.dvnr_launch_count() - l0
     clk = clocks.stop()
-    samples = n * w["batch"] * args.steps * world
+    samples = len(boxes_all) * w["batch"] * args.steps  # all ranks together
     res = {
         "metric": "INR train samples/s and decode samples/s at equal PSNR vs plain FP32 path",
         "value": samples / (ms / 1e3), "unit": "train samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f16",
         "data": "synthetic (seeded random-phase k^-5/3 spectral field)",
-        "config": {"workload": w["desc"], "models": n, "global_batch": n * w["batch"] * world,
-                   "parallelism": "64 independent partition models in one grouped launch per GPU",
-                   "l2": "working set > L2 (no flush needed)"},
-        "clocks": clk, "gpu_launches": int(launches)}
-    if rank != 0 or args.no_extras:
-        return res
-    hbm, have = _peaks()
-    A.call("dvnr_profile_enable", 1)
-    dv.train(models, vols, cfg(min(args.steps, 20)))
-    kern = _profile(A, ["train_fused_fp16", "mp_schedule", "adam", "minmax"])
-    A.call("dvnr_profile_enable", 0)
-    res["roofline"] = _roofline(kern, w, models[0].n_params * n, n * w["batch"], hbm, have)
-    if args.legs == "roofline":  # the roofline leg alone (profiling)
-        return res
+        "config": {"workload": w["desc"], "models": len(boxes_all), "models_this_rank": n,
+                   "global_batch": len(boxes_all) * w["batch"],
+                   "parallelism": f"64 partition models split over {world} GPU(s) by LPT on voxel "
+                                  "count, one grouped launch per step per GPU",
+                   "l2": "working set > L2 (no flush needed)",
+                   "warmup_extra": f"one untimed call of {args.steps} steps after the warm-up "
+                                   "(captures the step graphs the timed call replays)"},
+        "clocks": clk, "gpu_launches": int(launches),
+        "graph": {"captures_in_timed_region": g1[0] - g0[0], "graph_launches": g1[1] - g0[1],
+                  "eager_steps": g1[2] - g0[2]}}
+    if args.no_extras:
+        return res if rank == 0 else None
+    if rank == 0:
+        hbm, have = _peaks()
+        A.call("dvnr_profile_enable", 1)
+        dv.train(models, vols, cfg(min(args.steps, 20)))
+        kern = _profile(A, ["train_fused_fp16", "mp_schedule", "adam", "minmax"])
+        A.call("dvnr_profile_enable", 0)
+        res["roofline"] = _roofline(kern, w, models[0].n_params * n, n * w["batch"], hbm, have)
+        if args.legs == "roofline" and not compact:  # the roofline leg alone (profiling)
+            return res
     # full training from fresh models, then decode and PSNR over owned voxels
-    for i, m in enumerate(models):
+    for m in models:
         m.close()
-    models = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
+    models = fresh()
     # end to end: the blocks (with ghosts) come from pinned host memory inside
     # the timed region, as a simulation rank would hand them over
     pinned = [v.cpu().pin_memory() for v in vols]
@@ -482,7 +570,7 @@ def run_blocks(args, rank, world, local_rank):
     for dst, src in zip(dvols, pinned):
         dst.copy_(src, non_blocking=True)
     dv.train(models, dvols, cfg(w["steps_full"]))
-    t_full = time.perf_counter() - t0
+    t_full = shard.max_over_ranks(time.perf_counter() - t0)
     del dvols, pinned
     torch.cuda.synchronize()
     d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -492,43 +580,85 @@ def run_blocks(args, rank, world, local_rank):
         m.decode_grid(g)
     d1.record(stream)
     torch.cuda.synchronize()
-    dec_ms = d0.elapsed_time(d1)
-    sse, vox = 0.0, 0
-    for (lo, hi), g in zip(boxes, grids):
-        ref = field[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].contiguous()
-        s_, _ = dv.error_stats(g, ref)
-        sse += s_
-        vox += g.numel()
-    psnr = 10 * math.log10(1.0 / (sse / vox))
-    res["decode"] = {"value": vox / (dec_ms / 1e3), "unit": "decode samples/s", "ms": dec_ms,
-                     "points": vox}
-    res["psnr"] = {"path": psnr, "steps": w["steps_full"], "voxel_weighted": True}
-    res["e2e"] = {"value": n * w["batch"] * w["steps_full"] / t_full, "unit": "train samples/s",
-                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4 * n,
-                  "step": f"upload the 64 blocks, {w['steps_full']} grouped iterations of all 64 models, "
+    dec_ms = shard.max_over_ranks(d0.elapsed_time(d1))
+
+    def block_sse(grids_):
+        sse, vox = 0.0, 0
+        for (lo, hi), g in zip(boxes, grids_):
+            ref = field[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]].contiguous()
+            s_, _ = dv.error_stats(g, ref)
+            sse += s_
+            vox += g.numel()
+        return sse, vox
+
+    sse, vox = block_sse(grids)
+    psnr, _, vox_all = shard.global_psnr(sse, vox)
+    res["decode"] = {"value": vox_all / (dec_ms / 1e3), "unit": "decode samples/s", "ms": dec_ms,
+                     "points": int(vox_all)}
+    res["e2e"] = {"value": len(boxes_all) * w["batch"] * w["steps_full"] / t_full,
+                  "unit": "train samples/s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 4 * n,
+                  "step": f"upload the blocks, {w['steps_full']} grouped iterations of all models, "
                           "read losses"}
+    # the same blocks through the plain FP32 path (one model after another),
+    # full length, for the equal-PSNR comparison
+    f32 = fresh()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dv.train(f32, vols, cfg(w["steps_full"], A.DVNR_FP32))
+    t32 = shard.max_over_ranks(time.perf_counter() - t0)
+    g32 = [m.decode_grid() for m in f32]
+    sse32, _ = block_sse(g32)
+    psnr32, _, _ = shard.global_psnr(sse32, vox)
+    del g32
+    for m in f32:
+        m.close()
+    res["psnr"] = {"path": psnr, "fp32_path": psnr32, "delta_db": psnr - psnr32,
+                   "equal_psnr": abs(psnr - psnr32) <= 0.2, "gate_db": 0.2,
+                   "steps": w["steps_full"], "voxel_weighted": True}
+    v32 = len(boxes_all) * w["batch"] * w["steps_full"] / t32
+    res["fp32_path"] = {"value": v32, "unit": "train samples/s", "speedup": res["e2e"]["value"] / v32,
+                        "note": "both full 2000-iteration calls, host upload included on the FP16 side"}
+    # the frame of all blocks: each rank marches its blocks in the global
+    # frame one depth layer at a time, the layers of all ranks are gathered
+    # and blended front to back (sort-last, Sec. 4.3)
+    tf = dv.make_tf(alpha_max=0.05)
+    lo_f, hi_f = (0, 0, 0), (512, 512, 512)
+    layers = sorted({lo[2] for lo, _ in boxes_all})
+    torch.cuda.synchronize()
+    r0 = time.perf_counter()
+
+    def render_layer(z):
+        sel = [m for m, (lo, _) in zip(models, boxes) if lo[2] == z]
+        if not sel:
+            return torch.zeros((512, 512, 4), device=dev)
+        return dv.render_in_frame(sel, lo_f, hi_f, tf, 512, 512, 256)
+
+    img = shard.sort_last_frame(layers, render_layer, lambda ims, ds: dv.composite(ims, ds))
+    torch.cuda.synchronize()
+    res["render"] = {"ms": shard.max_over_ranks((time.perf_counter() - r0) * 1e3),
+                     "image": [512, 512], "samples_per_ray": 256,
+                     "composite": f"{len(layers)} depth layers x {world} rank(s), sort-last",
+                     "alpha_mean": float(img[..., 3].mean())}
+    if rank != 0:
+        return None
+    if compact:
+        for k in ("metric", "n_gpus", "higher_is_better", "vs_baseline", "data"):
+            res.pop(k, None)
+        return res
     # iteration budget proportional to each block's voxel count (Sec. 3.2,
     # N_epoch = 16), then the same with the early stop at the median of the
     # moving-average losses that run ended with: models leave the grouped
     # launch at different steps
     res["adaptive_budget"] = adaptive_budget(models, vols, boxes, enc, mlp, w, rank)
-    # plain FP32 path on the same blocks (one model after another), throughput only
-    f32 = [dv.Model(lo, hi, 1, enc, mlp, seed=100 + i) for i, (lo, hi) in enumerate(boxes)]
-    dv.train(f32, vols, cfg(3, A.DVNR_FP32))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    dv.train(f32, vols, cfg(20, A.DVNR_FP32))
-    t32 = time.perf_counter() - t0
-    res["fp32_path"] = {"value": n * w["batch"] * 20 / t32, "unit": "train samples/s",
-                        "speedup": (n * w["batch"] * 20 / t32) and res["value"] / (n * w["batch"] * 20 / t32)}
     res["cpu_baseline"] = cpu_baseline(w, vols[0].cpu().numpy())
     return res
 
 
-def run_insitu(args, rank, world, local_rank):
+def insitu_measure(args, rank, world, local_rank, compact=False):
     """In situ time series: each step of an advected 512^3 field is compressed
     by an INR warm-started from the previous step's weights (Sec. 3.5),
-    decoded back to the grid and ray-marched."""
+    decoded back to the grid and ray-marched. compact: the sub-object of the
+    default run (per-step figures summarised)."""
     import torch
 
     from paper_2304_10516_gb300 import _abi as A
@@ -635,6 +765,12 @@ def run_insitu(args, rank, world, local_rank):
                         "simulation sharing the GPU"},
         "per_step": per,
     }
+    if compact:
+        ps = [r["psnr"] for r in per]
+        res["psnr"] = {"min": min(ps), "max": max(ps), "mean": statistics.fmean(ps)}
+        res["push_ms"] = {"min": min(r["push_ms"] for r in per), "max": max(r["push_ms"] for r in per)}
+        for k in ("metric", "n_gpus", "higher_is_better", "vs_baseline", "data", "per_step"):
+            res.pop(k, None)
     return res
 
 
@@ -713,16 +849,25 @@ def adaptive_budget(models, vols, boxes, enc, mlp, w, rank):
     return out
 
 
-def learned_gain(model, untrained, vol):
-    """PSNR of the trained INR vs the untrained one and vs a grid of the same
-    FP16 byte budget (downsampled and read back by trilinear interpolation,
-    voxel centres aligned): the memory the representation saves and what that
-    memory buys when spent on a plain grid instead."""
-    import torch
+def _grid_same_bytes(vol, n_bytes):
+    """PSNR of the raw-grid fallback at n_bytes of FP16: the volume
+    downsampled to that many voxels and read back trilinearly (voxel centres
+    aligned)."""
     import torch.nn.functional as Fn
 
-    from paper_2304_10516_gb300 import model as dv
+    side = int(math.floor((n_bytes / 2) ** (1.0 / 3.0)))
+    v5 = vol[None, None]
+    small = Fn.interpolate(v5, size=(side,) * 3, mode="trilinear", align_corners=True).half().float()
+    back = Fn.interpolate(small, size=tuple(vol.shape), mode="trilinear", align_corners=True)[0, 0]
+    return back.contiguous(), side
 
+
+def learned_gain(model, untrained, vol, dv, w, new_model, cfg):
+    """PSNR of the trained INR vs the untrained one and vs a grid of the same
+    FP16 byte budget (the fallback): the memory the representation saves and
+    what that memory buys when spent on a plain grid instead. Then the same
+    comparison over the table size T and the step count, to show where the
+    learned representation overtakes the fallback."""
     def psnr_of(dec):
         sse, mx = dv.error_stats(dec, vol)
         return 10 * math.log10(1.0 / (sse / vol.numel())), mx
@@ -730,28 +875,39 @@ def learned_gain(model, untrained, vol):
     p_inr, mx_inr = psnr_of(model.decode_grid())
     p_init, _ = psnr_of(untrained.decode_grid())
     inr_bytes = model.n_params * 2
-    side = int(math.floor((inr_bytes / 2) ** (1.0 / 3.0)))
-    v5 = vol[None, None]
-    small = Fn.interpolate(v5, size=(side,) * 3, mode="trilinear", align_corners=True).half().float()
-    back = Fn.interpolate(small, size=tuple(vol.shape), mode="trilinear", align_corners=True)[0, 0]
-    p_grid, mx_grid = psnr_of(back.contiguous())
+    back, side = _grid_same_bytes(vol, inr_bytes)
+    p_grid, mx_grid = psnr_of(back)
     model.close()
     untrained.close()
     raw = vol.numel() * 4
-    return {"inr_bytes_fp16": inr_bytes, "raw_bytes_fp32": raw, "compression_ratio": raw / inr_bytes,
-            "psnr_inr": p_inr, "max_abs_inr": mx_inr, "psnr_untrained": p_init,
-            "psnr_grid_same_bytes": p_grid, "max_abs_grid_same_bytes": mx_grid,
-            "grid_side_same_bytes": side}
+    out = {"inr_bytes_fp16": inr_bytes, "raw_bytes_fp32": raw, "compression_ratio": raw / inr_bytes,
+           "psnr_inr": p_inr, "max_abs_inr": mx_inr, "psnr_untrained": p_init,
+           "psnr_grid_same_bytes": p_grid, "max_abs_grid_same_bytes": mx_grid,
+           "grid_side_same_bytes": side}
+    curve = []
+    for log2T, steps in ((19, 8000), (18, 2000), (17, 2000), (16, 2000), (16, 8000)):
+        enc = dv.EncodingConfig(w["L"], w["F"], log2T, w["base"], w["growth"])
+        m = new_model(100, enc)
+        dv.train([m], [vol], cfg(steps), sync=True)
+        p, _ = psnr_of(m.decode_grid())
+        b = m.n_params * 2
+        g, gs = _grid_same_bytes(vol, b)
+        pg, _ = psnr_of(g)
+        curve.append({"log2_T": log2T, "steps": steps, "inr_bytes_fp16": b,
+                      "compression_ratio": raw / b, "psnr_inr": p, "psnr_grid_same_bytes": pg,
+                      "gain_db": p - pg, "grid_side": gs})
+        m.close()
+    out["curve"] = curve
+    return out
 
 
-def cpu_baseline(w, vol_np, budget_s=12.0):
-    import oracle as orc
-
+def _oracle_steps(orc, w, vol_np, batch, budget_s, max_steps):
+    """FP64 training iterations of the workload's model at `batch` until
+    budget_s of wall time (at least one); returns (steps, seconds)."""
     oc = orc.Config(w["L"], w["F"], w["log2T"], w["base"], w["growth"], w["width"], w["hidden"])
     th = orc.init_params(oc, 100)
     m1, m2 = np.zeros_like(th), np.zeros_like(th)
-    batch = min(w["batch"], 1 << 15)
-    tc = orc.TrainConfig(batch=batch, lr=w["lr"], seed=7)
+    tc = orc.TrainConfig(batch=batch, lr=w["lr"], seed=7, lambda_bnd=w["lam"])
     st = orc.State()
     vmin, vmax = float(vol_np.min()), float(vol_np.max())
     t0 = time.perf_counter()
@@ -759,17 +915,40 @@ def cpu_baseline(w, vol_np, budget_s=12.0):
     while True:
         orc.train(oc, tc, st, th, m1, m2, vol_np, vmin, vmax, 1)
         steps += 1
-        if time.perf_counter() - t0 > budget_s or steps >= 50:
+        if time.perf_counter() - t0 > budget_s or steps >= max_steps:
             break
-    dt = time.perf_counter() - t0
-    return {"value": steps * batch / dt, "unit": "train samples/s", "cores": orc.threads(),
-            "kind": "oracle",
-            "sample": f"{steps} FP64 training iterations of the same model at batch {batch} "
-                      f"(Adam over all {oc.n_params} parameters each iteration)"}
+    return steps, time.perf_counter() - t0, oc.n_params
+
+
+def cpu_baseline(w, vol_np, budget_s=12.0):
+    """The FP64 oracle on the host cores at the workload's own batch (all
+    cores), and single-threaded on a smaller batch."""
+    import oracle as orc
+
+    cores = orc.set_threads(os.cpu_count() or 1)
+    steps, dt, P = _oracle_steps(orc, w, vol_np, w["batch"], budget_s, 50)
+    out = {"value": steps * w["batch"] / dt, "unit": "train samples/s", "cores": cores,
+           "kind": "oracle",
+           "sample": f"{steps} FP64 training iterations of the same model at the full batch "
+                     f"{w['batch']} (Adam over all {P} parameters each iteration), {dt:.1f} s"}
+    b1 = min(w["batch"], 1 << 12)
+    orc.set_threads(1)
+    try:
+        s1, d1, _ = _oracle_steps(orc, w, vol_np, b1, 5.0, 50)
+    finally:
+        orc.set_threads(cores)
+    out["single_thread"] = {"value": s1 * b1 / d1, "unit": "train samples/s", "cores": 1,
+                            "sample": f"{s1} FP64 training iterations at batch {b1} "
+                                      f"(Adam over all {P} parameters each iteration), {d1:.1f} s"}
+    return out
 
 
 # ------------------------------------------------------ reference arm ------
 def run_reference(args):
+    """The FP64 oracle timed on the host cores on the workload of our arm:
+    the same model, volume and batch (2^18 for the 256^3 workload) while the
+    whole run stays within about 60 full steps; beyond that the batch is
+    scaled down by a power of two and the sample says so."""
     import oracle as orc
 
     from paper_2304_10516_gb300 import volumes
@@ -780,17 +959,22 @@ def run_reference(args):
     oc = orc.Config(w["L"], w["F"], w["log2T"], w["base"], w["growth"], w["width"], w["hidden"])
     th = orc.init_params(oc, 100)
     m1, m2 = np.zeros_like(th), np.zeros_like(th)
-    batch = min(w["batch"], 1 << 13)
-    tc = orc.TrainConfig(batch=batch, lr=w["lr"], seed=7)
+    total = args.steps + max(args.warmup, 1)
+    batch = w["batch"]
+    while batch > 1024 and total * batch > 60 * w["batch"]:
+        batch //= 2
+    tc = orc.TrainConfig(batch=batch, lr=w["lr"], seed=7, lambda_bnd=w["lam"])
     st = orc.State()
+    cores = orc.set_threads(os.cpu_count() or 1)
     vmin, vmax = float(vol_np.min()), float(vol_np.max())
     orc.train(oc, tc, st, th, m1, m2, vol_np, vmin, vmax, max(args.warmup, 1))
     t0 = time.perf_counter()
     orc.train(oc, tc, st, th, m1, m2, vol_np, vmin, vmax, args.steps)
     dt = time.perf_counter() - t0
     value = args.steps * batch / dt
-    sample = (f"each step one FP64 training iteration of the same model at batch {batch} "
-              f"(a bounded sample of the {w['batch']}-sample step)")
+    sample = (f"each step one FP64 training iteration of the same model at batch {batch}"
+              + (" (the full step)" if batch == w["batch"] else
+                 f" (a bounded sample of the {w['batch']}-sample step)"))
     return {
         "impl": "reference", "metric": "INR train samples/s and decode samples/s at equal PSNR "
         "vs plain FP32 path", "value": value, "unit": "train samples/s", "n_gpus": 1,
@@ -798,7 +982,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded random-phase k^-5/3 spectral field)",
         "config": {"workload": w["desc"], "global_batch": batch, "parallelism": "1 CPU process"},
-        "cpu_baseline": {"value": value, "unit": "train samples/s", "cores": orc.threads(),
+        "cpu_baseline": {"value": value, "unit": "train samples/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "train samples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -822,9 +1006,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.workload == "blocks64":
-        res = run_blocks(args, rank, world, local_rank)
+        res = blocks_measure(args, rank, world, local_rank)
     elif args.workload == "insitu512":
-        res = run_insitu(args, rank, world, local_rank)
+        res = insitu_measure(args, rank, world, local_rank)
     else:
         res = run_ours(args, rank, world, local_rank)
     if rank == 0 and res is not None:

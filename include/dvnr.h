@@ -143,7 +143,8 @@ typedef struct {
   double last_loss;        /* mean loss of the last step                       */
   int64_t iter;            /* iterations drawn                                  */
   int64_t adam_t;          /* Adam steps applied                                */
-  int64_t skipped;         /* steps skipped for a non-finite gradient           */
+  int64_t skipped;         /* steps skipped: non-finite gradient, or a step     */
+                           /*   a bounded device wait aborted                   */
   int64_t n_enc, n_mlp;    /* parameter counts                                  */
   int32_t precision;       /* precision used by decode/render                   */
   int32_t nonfinite_input; /* 1 when the last training volume held NaN/Inf      */
@@ -248,8 +249,10 @@ dvnr_status dvnr_copy_weights(dvnr_model dst, dvnr_model src, void* stream);
  * training precision). Switching to FP16 refreshes the FP16 copy.          */
 dvnr_status dvnr_set_precision(dvnr_model m, int32_t precision, void* stream);
 
-/* Synchronous snapshot of the model state; reports DVNR_E_NONFINITE_INPUT
- * if the last training volume held NaN/Inf (state still filled in).        */
+/* Synchronous snapshot of the model state; reports DVNR_E_TIMEOUT if a
+ * bounded device wait gave up since the start of the last training call (in
+ * that call or in a decode after it), else DVNR_E_NONFINITE_INPUT if the last
+ * training volume held NaN/Inf (the state is filled in either way).        */
 dvnr_status dvnr_get_state(dvnr_model m, dvnr_state_info* out);
 
 /* Set the value range that decoding de-normalises with (Sec. 4.1: outputs
@@ -298,6 +301,29 @@ dvnr_status dvnr_train(dvnr_model* models, int32_t n,
 dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev,
                             const dvnr_train_cfg* cfg, int64_t iteration,
                             const dvnr_step_outputs* out, void* stream);
+
+/* One Adam step (Sec. 3.6: beta1, beta2, eps, L2 weight decay added to the
+ * gradient, Kingma & Ba bias correction) from a gradient the caller supplies
+ * instead of one training step's: grad_dev holds n_enc + n_mlp float32 values
+ * on the device in the compact layout of dvnr_get_weights, the gradient of the
+ * loss (not loss-scaled). Uses cfg->lr, beta1, beta2, eps, weight_decay and
+ * precision (and cfg->batch for the FP16 path's initial loss scale when the
+ * model has none yet). The same fused optimiser kernel as dvnr_train: the FP32
+ * master weights, both moments and the FP16 copy are updated and the gradient
+ * buffer is cleared. FP16 precision: the gradient is multiplied by the loss
+ * scale S before the step (Adam divides it out); a value that is or becomes
+ * non-finite skips the step and halves S, and growth_interval finite steps
+ * double it, as in training. FP32 precision: S = 1; a non-finite value skips
+ * the step. The iteration count, the last loss and its moving average are
+ * not changed. Asynchronous on `stream`. Errors: DVNR_E_INVALID,
+ * DVNR_E_STATE (frozen model), DVNR_E_UNSUPPORTED, DVNR_E_CUDA.             */
+dvnr_status dvnr_adam_step(dvnr_model m, const float* grad_dev, const dvnr_train_cfg* cfg,
+                           void* stream);
+
+/* Copy the Adam moments (first m1, second m2; FP32) to host memory in the
+ * compact layout of dvnr_get_weights, n = n_enc + n_mlp each; either pointer
+ * may be NULL. Synchronises the device. DVNR_E_STATE for a frozen model.    */
+dvnr_status dvnr_get_moments(dvnr_model m, float* m1_host, float* m2_host, int64_t n);
 
 /* Point inference (Sec. 3, Sec. 4.1): n points in global voxel coordinates
  * (x, y, z float32 triples; voxel centre of global index j is at j) mapped
@@ -447,6 +473,30 @@ dvnr_status dvnr_profile_read(const char* kernel, double* total_ms, int64_t* lau
  * device: they are included once the stream that ran them has been
  * synchronised.                                                            */
 int64_t dvnr_launch_count(void);
+
+/* How the FP16 grouped training has run its steps since the library was
+ * loaded: CUDA graphs captured (each also instantiated), graph launches, and
+ * steps launched directly (each pointer may be NULL). A call of n steps
+ * replays graphs of 32 steps, then of 16 and 8 for the binary digits of the
+ * rest, each captured on its first use for the call's models and settings;
+ * fewer than 8 remaining steps run directly, as does every step while
+ * profiling or a lowered wait limit is active. The early-stop loop graph
+ * counts one launch per call. Host counters, no synchronisation.           */
+dvnr_status dvnr_graph_stats(int64_t* captures, int64_t* replays, int64_t* eager_steps);
+
+/* Diagnostic for tests of the failure path: the limit, in SM clocks, of the
+ * first tensor-core wait of every CTA of the FP16 training and decoding
+ * kernels (later waits keep theirs, about 2 s). cycles >= 0 sets it; 0 gives
+ * up unless the first product is complete when the CTA first looks, which
+ * makes that wait run out. -1 restores the default. On giving up a CTA lets
+ * its product finish (bounded wait), frees its tensor memory and returns; the
+ * model's step is skipped by Adam (parameters and moments unchanged, loss
+ * scale kept) and the call reports DVNR_E_TIMEOUT (dvnr_train with
+ * final_loss_host, dvnr_get_state). While a limit is set, FP16 training
+ * launches its steps directly (no CUDA graph, no launch-shape trials).
+ * Process-wide; *previous (may be NULL) receives the limit it replaces.
+ * DVNR_E_INVALID for cycles < -1.                                            */
+dvnr_status dvnr_debug_first_wait(int64_t cycles, int64_t* previous);
 
 /* Diagnostic of the tensor-core operand layouts used by the FP16 path: one
  * 128 x 64 x 64 tcgen05 product per operand order (A K-major/MN-major x

@@ -35,6 +35,19 @@ int orc_threads(void) {
 #endif
 }
 
+/* Threads of the parallel loops from now on (n >= 1); returns the number in
+ * effect afterwards. Timing only: results do not depend on it beyond the
+ * order of FP64 additions in the batch sums.                               */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Configuration. Level resolution N_l = floor(N_min * b^l) (Mueller et al.,
  * Eq. 2-3; the DVNR paper defers to that paper in Sec. 3). A level is stored

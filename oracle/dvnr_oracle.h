@@ -177,6 +177,7 @@ void orc_render_inr(const orc_cfg* c, int32_t n_blocks, const double* const* the
 double orc_mse(const double* a, const float* b, int64_t n, double* max_abs);
 
 int  orc_threads(void);
+int  orc_set_threads(int n);
 
 #ifdef __cplusplus
 }

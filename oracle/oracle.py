@@ -133,6 +133,8 @@ def _lib_handle():
             lib.orc_mse.argtypes = [_P, _P, C.c_int64, _P]
             lib.orc_mse.restype = C.c_double
             lib.orc_threads.restype = C.c_int
+            lib.orc_set_threads.argtypes = [C.c_int]
+            lib.orc_set_threads.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -415,3 +417,8 @@ def mse(a, b):
 
 def threads():
     return int(_lib_handle().orc_threads())
+
+
+def set_threads(n):
+    """Threads of the oracle's parallel loops (timing only); returns the count in effect."""
+    return int(_lib_handle().orc_set_threads(int(n)))

@@ -31,7 +31,8 @@ EXPORTS = [
     "dvnr_error_stats_noalloc", "dvnr_export_fp16", "dvnr_import_fp16", "dvnr_render_inr",
     "dvnr_adaptive_encoding", "dvnr_freeze", "dvnr_window_create", "dvnr_window_destroy",
     "dvnr_window_push", "dvnr_window_range", "dvnr_window_model", "dvnr_window_bytes",
-    "dvnr_render_in_frame", "dvnr_composite", "dvnr_set_value_range",
+    "dvnr_render_in_frame", "dvnr_composite", "dvnr_set_value_range", "dvnr_adam_step",
+    "dvnr_get_moments", "dvnr_debug_first_wait", "dvnr_graph_stats",
 ]
 
 
@@ -125,6 +126,10 @@ _SIGS = {
     "dvnr_selftest_umma": ([_P], C.c_int),
     "dvnr_error_stats_noalloc": ([_P, _P, C.c_int64, _P, _P], C.c_int),
     "dvnr_export_fp16": ([_P, _P, C.c_int64], C.c_int),
+    "dvnr_adam_step": ([_P, _P, C.POINTER(dvnr_train_cfg), _P], C.c_int),
+    "dvnr_get_moments": ([_P, _P, _P, C.c_int64], C.c_int),
+    "dvnr_debug_first_wait": ([C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "dvnr_graph_stats": ([C.POINTER(C.c_int64)] * 3, C.c_int),
     "dvnr_import_fp16": ([_P, _P, C.c_int64], C.c_int),
 }
 

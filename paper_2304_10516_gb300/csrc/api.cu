@@ -187,6 +187,7 @@ AdamHyper adam_hyper(const dvnr_train_cfg* cfg, bool mixed) {
   h.gated = 1;
   h.stop_loss = cfg->stop_loss;
   h.stop_decay = cfg->stop_decay;
+  h.external = 0;
   return h;
 }
 
@@ -739,6 +740,51 @@ dvnr_status dvnr_train_grad(dvnr_model m, const float* vol_dev, const dvnr_train
   }
   if (rc != DVNR_OK) return rc;
   return launch_finish_grad(m, S, 1.0f / (float)cfg->batch, o.grad, o.loss, s);
+}
+
+dvnr_status dvnr_adam_step(dvnr_model m, const float* grad_dev, const dvnr_train_cfg* cfg,
+                           void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_adam_step");
+  g_err[0] = 0;
+  if (!m || !grad_dev) return fail(DVNR_E_INVALID, "NULL model or gradient");
+  if (m->frozen) return fail(DVNR_E_STATE, "the model is frozen");
+  dvnr_status rc = check_train_cfg(cfg);
+  if (rc != DVNR_OK) return rc;
+  const bool mixed = cfg->precision == DVNR_FP16;
+  if (mixed && !mp_supported(m))
+    return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
+  if ((rc = use_device(m)) != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (mixed && !m->scale_initialized) {
+    if ((rc = launch_state_reset_scale(m->st, initial_loss_scale(cfg->batch), s)) != DVNR_OK) return rc;
+    m->scale_initialized = true;
+  }
+  if ((rc = launch_load_grad(m, grad_dev, mixed, s)) != DVNR_OK) return rc;
+  AdamHyper h = adam_hyper(cfg, mixed);
+  h.gated = 0;  // not bound to a training call's budget
+  h.external = 1;
+  h.stop_loss = 0.f;
+  if ((rc = launch_adam(adam_ptrs_dev(m), 1, m->n_store, h, s)) != DVNR_OK) return rc;
+  m->precision = cfg->precision;
+  return DVNR_OK;
+}
+
+dvnr_status dvnr_get_moments(dvnr_model m, float* m1_host, float* m2_host, int64_t n) {
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (m->frozen) return fail(DVNR_E_STATE, "a frozen model keeps no optimiser state");
+  if (n != m->n_params) return fail(DVNR_E_INVALID, "n must equal n_enc + n_mlp = %lld", (long long)m->n_params);
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  DVNR_CUDA(cudaDeviceSynchronize());
+  for (int b = 0; b <= m->lmap.L; ++b) {
+    const int64_t e0 = m->lmap.ext_off[b], len = m->lmap.ext_off[b + 1] - e0;
+    const int64_t i0 = m->lmap.int_off[b];
+    if (m1_host)
+      DVNR_CUDA(cudaMemcpy(m1_host + e0, m->m1 + i0, (size_t)len * 4, cudaMemcpyDeviceToHost));
+    if (m2_host)
+      DVNR_CUDA(cudaMemcpy(m2_host + e0, m->m2 + i0, (size_t)len * 4, cudaMemcpyDeviceToHost));
+  }
+  return DVNR_OK;
 }
 
 dvnr_status dvnr_decode_points(dvnr_model m, const float* xyz_dev, int64_t n, float* out_dev,

@@ -46,6 +46,10 @@ struct ProfScope {
 };
 bool profiling_on();
 void count_launches(int64_t n);
+// dvnr_graph_stats counters of the grouped training's step graphs
+void count_graph_capture();
+void count_graph_replay();
+void count_eager_steps(int64_t n);
 // An NVTX range named after a public call, open for the call's duration (a
 // host-side marker for profilers; without an attached tool it costs a
 // branch).
@@ -92,10 +96,16 @@ __host__ __device__ inline int64_t ext_to_int(const LayoutMap& lm, int64_t i) {
 // ------------------------------------------------------- device state ------
 // Per-model state that lives on the device so that whole training steps can
 // be captured in a CUDA graph and replayed.
+// Bits of ModelState::overflow: the step's gradient is unusable and Adam
+// skips the step (and clears the gradient). A non-finite gradient also halves
+// the FP16 loss scale; an aborted step (a bounded wait gave up) does not.
+constexpr uint32_t kNonFiniteGrad = 1u;
+constexpr uint32_t kStepAborted = 2u;
+
 struct ModelState {
   uint32_t enc_min, enc_max;  // order-preserving encodings of the value range
   uint32_t nonfinite;         // training volume held NaN/Inf
-  uint32_t overflow;          // a non-finite gradient was produced this step
+  uint32_t overflow;          // kNonFiniteGrad | kStepAborted of this step
   float loss_scale;           // dynamic loss scale S (FP16 path)
   uint32_t good_steps;        // finite steps since the last scale change
   uint32_t iter;              // iterations drawn (Philox counter word 1)
@@ -364,6 +374,10 @@ dvnr_status launch_init_params(dvnr_model m, uint64_t seed, cudaStream_t s);
 dvnr_status launch_refresh_half(dvnr_model m, cudaStream_t s);
 dvnr_status launch_widen_half(dvnr_model m, cudaStream_t s);
 dvnr_status launch_begin_call(ModelState* st, uint32_t budget, cudaStream_t s);
+// Load a caller-given gradient (compact layout, unscaled) into the model's
+// gradient buffer as Adam expects it: times the loss scale on the FP16 path,
+// a non-finite value flagged as kNonFiniteGrad.
+dvnr_status launch_load_grad(dvnr_model m, const float* grad_in, bool mixed, cudaStream_t s);
 dvnr_status launch_minmax(const float* vol, int64_t n, ModelState* st, cudaStream_t s);
 dvnr_status launch_error_stats(const float* a, const float* b, int64_t n, double* out_dev,
                                cudaStream_t s);
@@ -384,6 +398,10 @@ struct AdamHyper {
   int32_t mixed, growth_interval;
   int32_t gated;               // skip models that are not model_active
   float stop_loss, stop_decay; // early stop (stop_loss 0: off)
+  // the gradient came from the caller (dvnr_adam_step): no samples were
+  // drawn and no loss was taken, so the iteration count, the last loss and
+  // its moving average stay as they are
+  int32_t external;
 };
 dvnr_status launch_adam(const AdamModelPtrs* models_dev, int n_models, int64_t n_params,
                         const AdamHyper& h, cudaStream_t s);

@@ -30,6 +30,7 @@
 // the 128 features starting at dZ_{k+1}; rows W..127 of that accumulator
 // collect unused products and are never read.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -48,6 +49,17 @@ namespace {
 #ifndef DVNR_TRAIN_STAGED
 #define DVNR_TRAIN_STAGED 1
 #endif
+// Step graphs of the grouped training: 2^kMaxGraphLog steps per replay (and
+// per body run of the early-stop loop); the fixed graphs of a call's
+// remaining steps have 2^k steps, k >= kMinGraphLog (fewer steps run eagerly:
+// their capture would cost more than it saves)
+constexpr int kMaxGraphLog = 5;
+constexpr int kMinGraphLog = 3;
+
+// Limit of each CTA's first tensor-core wait in the training and decoding
+// kernels (dvnr_debug_first_wait); kWaitCycles unless a test lowers it.
+std::atomic<long long> g_first_wait{kWaitCycles};
+
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
 [[maybe_unused]] constexpr int kTrainKernelRevision = 10;
@@ -88,6 +100,9 @@ struct MpParams {
   // inactive), written by k_mp_schedule; nullptr = all n_models take part
   const int32_t* sched;
   int32_t n_models;
+  // limit of each CTA's first tensor-core wait (SM clocks; <= 0: give up
+  // unless complete at once); later waits use kWaitCycles
+  long long first_wait_cycles;
 };
 
 struct MpDecodeParams {
@@ -110,6 +125,7 @@ struct MpDecodeParams {
   // the launch's divisors: e[0], e[1] (grid point -> voxel), 2 (nstore[a] - 1)
   // (voxel -> fixed point), nr and rb.npx (ray lattice)
   FastDiv div_e0, div_e1, div_fix[3], div_nr, div_npx;
+  long long first_wait_cycles;  // as MpParams
 };
 
 // One 16-column chunk of dL/d(encoding) (levels c/F .. c/F + 16/F - 1); with
@@ -251,9 +267,14 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
   float acc_out[NOUT];
   float loss_acc = 0.f;
 
+  // thread 0: an MMA was committed and its completion not yet seen by
+  // thread 0 (after an abort, teardown waits for it before freeing TMEM)
+  bool inflight = false;
+  long long wait_limit = p.first_wait_cycles;
   // wait for the tensor core and raise/observe the CTA-wide abort flag
   auto mma_wait = [&]() -> bool {
-    umma::mbar_wait_bounded(mbar, phase, abort_flag, kWaitCycles);
+    if (umma::mbar_wait_bounded(mbar, phase, abort_flag, wait_limit)) inflight = false;
+    wait_limit = kWaitCycles;
     phase ^= 1u;
     __syncthreads();
     return *abort_flag == 0u;
@@ -372,6 +393,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
         umma::fence_after_sync();
         issue_forward(tmem, smem, p.lay, k, k == 0 ? (int)p.lay.dpad : W, W);
         umma::commit(mbar);
+        inflight = true;
       }
       if (!mma_wait()) goto teardown;
       umma::fence_after_sync();
@@ -506,6 +528,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
             umma::mma_f16(tmem, a, b, ibw, kk > 0);
           }
           umma::commit(mbar);
+          inflight = true;
         }
         if (!mma_wait()) goto teardown;
         umma::fence_after_sync();
@@ -555,12 +578,21 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
 
 teardown:
   if (*abort_flag) {
-    // give an MMA still in flight a bounded chance to finish before freeing TMEM
     if (tid == 0) {
-      const long long t0 = clock64();
-      while (!umma::mbar_try_wait(mbar, phase) && clock64() - t0 < kWaitCycles) {
+      // give the MMA whose wait gave up a bounded chance to finish before
+      // TMEM is freed: its phase is the one before `phase` (flipped on exit
+      // from the wait)
+      if (inflight) {
+        const long long t0 = clock64();
+        while (!umma::mbar_try_wait(mbar, phase ^ 1u) && clock64() - t0 < kWaitCycles) {
+        }
       }
-      if (cur >= 0) atomicAdd(&md.st->timeouts, 1u);
+      // the step of this model is incomplete: count the timeout and have Adam
+      // skip the step (kStepAborted), which also clears the partial gradient
+      if (cur >= 0) {
+        atomicAdd(&md.st->timeouts, 1u);
+        atomicOr(&md.st->overflow, kStepAborted);
+      }
     }
   }
   umma::fence_before_sync();
@@ -655,6 +687,8 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
   const uint32_t tmem = *tmem_slot;
   const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
   uint32_t phase = 0;
+  bool inflight = false;  // thread 0, as in k_mp_train
+  long long wait_limit = p.first_wait_cycles;
   float vmin, inv_range;
   value_range(p.st, vmin, inv_range);
   const float range = inv_range > 0.f ? ordered_to_float(p.st->enc_max) - vmin : 0.f;
@@ -698,8 +732,10 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
         umma::fence_after_sync();
         issue_forward(tmem, smem, p.lay, k, k == 0 ? (int)p.lay.dpad : W, W);
         umma::commit(mbar);
+        inflight = true;
       }
-      umma::mbar_wait_bounded(mbar, phase, abort_flag, kWaitCycles);
+      if (umma::mbar_wait_bounded(mbar, phase, abort_flag, wait_limit)) inflight = false;
+      wait_limit = kWaitCycles;
       phase ^= 1u;
       __syncthreads();
       if (*abort_flag) goto teardown;
@@ -742,8 +778,10 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
   }
 teardown:
   if (*abort_flag && tid == 0) {
-    const long long t0 = clock64();
-    while (!umma::mbar_try_wait(mbar, phase) && clock64() - t0 < kWaitCycles) {
+    if (inflight) {  // the MMA of the phase before `phase`
+      const long long t0 = clock64();
+      while (!umma::mbar_try_wait(mbar, phase ^ 1u) && clock64() - t0 < kWaitCycles) {
+      }
     }
     atomicAdd(const_cast<uint32_t*>(&p.st->timeouts), 1u);
   }
@@ -776,6 +814,7 @@ __global__ void __launch_bounds__(128) k_umma_selftest(int32_t* mismatches) {
   umma::fence_after_sync();
   const uint32_t tmem = tslot;
   uint32_t phase = 0;
+  bool inflight = false;  // thread 0: committed, completion not yet seen
   for (int cs = 0; cs < 4; ++cs) {
     const int a_mn = cs & 1, b_mn = cs >> 1;
     // A: M = 128, K = 64. K-major: core (m/8, k/8) at ((k/8)*16 + m/8)*128,
@@ -816,8 +855,9 @@ __global__ void __launch_bounds__(128) k_umma_selftest(int32_t* mismatches) {
         umma::mma_f16(tmem, a, b, id, kk > 0);
       }
       umma::commit(&bar);
+      inflight = true;
     }
-    umma::mbar_wait_bounded(&bar, phase, &abort_s, kWaitCycles);
+    if (umma::mbar_wait_bounded(&bar, phase, &abort_s, kWaitCycles)) inflight = false;
     phase ^= 1u;
     __syncthreads();
     if (abort_s) break;
@@ -839,7 +879,14 @@ __global__ void __launch_bounds__(128) k_umma_selftest(int32_t* mismatches) {
     umma::fence_before_sync();
     __syncthreads();
   }
-  if (abort_s && tid == 0) mismatches[4] = 1;
+  if (abort_s && tid == 0) {
+    mismatches[4] = 1;
+    if (inflight) {  // let the product of the phase before `phase` finish before TMEM is freed
+      const long long t0 = clock64();
+      while (!umma::mbar_try_wait(&bar, phase ^ 1u) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  }
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
@@ -885,17 +932,21 @@ struct MpCache {
   std::vector<uint32_t> slots;
   dvnr_train_cfg cfg{};
   int graph_steps = 0;
+  // fixed graphs of 2^k steps (k = kMinGraphLog .. kMaxGraphLog), captured on
+  // first use: a call of n steps replays the binary digits of n
+  cudaGraphExec_t fixed_exec[kMaxGraphLog + 1] = {};
+  cudaGraph_t fixed_graph[kMaxGraphLog + 1] = {};
   MpModel* d_models = nullptr;
   AdamModelPtrs* d_adam = nullptr;
   int32_t* d_sched = nullptr;  // active-model schedule, 1 + 2 n ints, then the loop's run count
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec = nullptr;  // the early-stop loop graph
   cudaGraph_t graph = nullptr;
   cudaStream_t cap = nullptr;
   int64_t wave_tiles = 0;
   int ctas_per_sm = 0;
   bool scheduled = false;  // the captured graph launches k_mp_schedule
   // early-stop graph: arm node -> WHILE { steps, k_mp_continue }
-  bool looped = false;          // exec is that graph
+  bool looped = false;          // exec holds the loop graph
   bool loop_unavailable = false;  // building it failed once: fixed graphs only
   cudaGraphNode_t arm_node = nullptr;
   cudaKernelNodeParams arm_params{};
@@ -908,11 +959,22 @@ struct MpCache {
   unsigned long long* arm_launches_dev = nullptr;
   int32_t arm_body = 0;
   cudaGraphConditionalHandle arm_cond = 0;
+  bool any_graph() const {
+    bool any = exec != nullptr;
+    for (int k = 0; k <= kMaxGraphLog; ++k) any |= fixed_exec[k] != nullptr;
+    return any;
+  }
   void drop_graph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
+    for (int k = 0; k <= kMaxGraphLog; ++k) {
+      if (fixed_exec[k]) cudaGraphExecDestroy(fixed_exec[k]);
+      if (fixed_graph[k]) cudaGraphDestroy(fixed_graph[k]);
+      fixed_exec[k] = nullptr;
+      fixed_graph[k] = nullptr;
+    }
     arm_node = nullptr;
     looped = false;
     graph_steps = 0;
@@ -920,7 +982,7 @@ struct MpCache {
   void clear() {
     // a graph of an earlier call may still run on another stream, writing
     // the launch counter and reading the descriptor tables
-    if (exec || arm_launches || d_models) cudaDeviceSynchronize();
+    if (any_graph() || arm_launches || d_models) cudaDeviceSynchronize();
     drop_graph();
     device_counter_free(arm_launches);
     arm_launches = nullptr;
@@ -962,6 +1024,7 @@ MpParams base_params(const dvnr_model m, const MpLayout& lay, const dvnr_train_c
   p.key = make_uint2((uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32));
   p.qtab = m->qtab;
   p.inv_batch = 1.0f / (float)cfg->batch;
+  p.first_wait_cycles = g_first_wait.load();
   return p;
 }
 
@@ -1240,7 +1303,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   {
     const char* at = getenv("DVNR_AUTOTUNE");
     const bool tune = !(at && atoi(at) == 0) && !getenv("DVNR_WAVE_MODELS") && !getenv("DVNR_WAVE_TILES") &&
-                      !profiling_on();
+                      !profiling_on() && p.first_wait_cycles == kWaitCycles;
     const std::string key = tune_key(m0, n, cfg);
     TuneChoice ch{0, 0};
     bool have = false;
@@ -1268,7 +1331,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
       set_waves(p, m0, n);
     }
   }
-  if (c->exec && (c->wave_tiles != p.wave_tiles || c->ctas_per_sm != p.lay.ctas_per_sm ||
+  if (c->any_graph() && (c->wave_tiles != p.wave_tiles || c->ctas_per_sm != p.lay.ctas_per_sm ||
                   c->scheduled != (p.sched != nullptr))) {
     DVNR_CUDA(cudaStreamSynchronize(s));
     c->drop_graph();
@@ -1284,67 +1347,85 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     return launch_adam(c->d_adam, n, m0->n_store, h, st);
   };
   int64_t left = steps;
-  if (profiling_on() || left < 8) {
+  // a lowered first-wait limit (failure-path tests) is not baked into graphs
+  if (profiling_on() || p.first_wait_cycles != kWaitCycles) {
+    count_eager_steps(left);
     for (int64_t i = 0; i < left; ++i) {
       dvnr_status rc = one_step(s);
       if (rc != DVNR_OK) return rc;
     }
     return DVNR_OK;
   }
-  const int G = 32;  // steps per graph replay (per body run of the early-stop loop)
+  const int G = 1 << kMaxGraphLog;
   // models that can leave the group (budgets, stop rule) run under the
   // early-stop loop, which ends when none is left; the others, or a driver
-  // without conditional nodes, replay a fixed graph of G steps (whose steps
-  // do nothing for models that left). DVNR_GRAPH_LOOP=0 selects the fixed
-  // graph for every call.
+  // without conditional nodes, replay fixed graphs (whose steps do nothing for
+  // models that left). DVNR_GRAPH_LOOP=0 selects the fixed graphs for every
+  // call.
   const char* gl = getenv("DVNR_GRAPH_LOOP");
-  const bool want_loop = p.sched != nullptr && !c->loop_unavailable && !(gl && atoi(gl) == 0);
-  if (c->exec && (c->graph_steps != G || c->looped != want_loop)) {
-    DVNR_CUDA(cudaStreamSynchronize(s));
-    c->drop_graph();
-  }
+  const bool want_loop = p.sched != nullptr && !c->loop_unavailable && !(gl && atoi(gl) == 0) && left >= 8;
   if (!c->cap) DVNR_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   if (!c->exec && want_loop) {
+    count_graph_capture();
     dvnr_status rc = build_loop_graph(c, p.models, n, c->d_sched + 1 + 2 * (size_t)n, G, one_step);
     if (rc != DVNR_OK) {
-      // conditional nodes unavailable: keep the fixed graph for this cache
-      c->drop_graph();
+      // conditional nodes unavailable: keep the fixed graphs for this cache
+      if (c->exec) cudaGraphExecDestroy(c->exec);
+      if (c->graph) cudaGraphDestroy(c->graph);
+      c->exec = nullptr;
+      c->graph = nullptr;
+      c->looped = false;
       c->loop_unavailable = true;
       cudaGetLastError();
       if (rc != DVNR_E_UNSUPPORTED) return rc;
     }
   }
-  if (!c->exec) {
-    set_capturing(true);
-    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
-    dvnr_status rc = DVNR_OK;
-    if (e == cudaSuccess) {
-      for (int g = 0; g < G && rc == DVNR_OK; ++g) rc = one_step(c->cap);
-      cudaError_t e2 = cudaStreamEndCapture(c->cap, &c->graph);
-      if (e == cudaSuccess) e = e2;
-    }
-    set_capturing(false);
-    if (rc != DVNR_OK) return rc;
-    DVNR_CUDA(e);
-    DVNR_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
-    c->graph_steps = G;
-    c->looped = false;
-  }
-  if (c->looped) {
+  if (c->exec && want_loop) {
     // at most ceil(steps / G) body runs: every model's budget is at most
     // `steps`, and the step slots past a model's budget or stop are no-ops
     const int64_t runs = (left + G - 1) / G;
     c->arm_value = (int32_t)std::min<int64_t>(runs, 0x7FFFFFFF);
     DVNR_CUDA(cudaGraphExecKernelNodeSetParams(c->exec, c->arm_node, &c->arm_params));
     DVNR_CUDA(cudaGraphLaunch(c->exec, s));
+    count_graph_replay();
     count_launches(1);  // the arm node; the body runs count themselves on the device
     return DVNR_OK;
   }
+  // the graph of 2^k steps, captured on first use
+  auto run_graph = [&](int k) -> dvnr_status {
+    if (!c->fixed_exec[k]) {
+      count_graph_capture();
+      set_capturing(true);
+      cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+      dvnr_status rc = DVNR_OK;
+      if (e == cudaSuccess) {
+        for (int g = 0; g < (1 << k) && rc == DVNR_OK; ++g) rc = one_step(c->cap);
+        cudaError_t e2 = cudaStreamEndCapture(c->cap, &c->fixed_graph[k]);
+        if (e == cudaSuccess) e = e2;
+      }
+      set_capturing(false);
+      if (rc != DVNR_OK) return rc;
+      DVNR_CUDA(e);
+      DVNR_CUDA(cudaGraphInstantiate(&c->fixed_exec[k], c->fixed_graph[k], 0));
+    }
+    DVNR_CUDA(cudaGraphLaunch(c->fixed_exec[k], s));
+    count_graph_replay();
+    count_launches((int64_t)(p.sched ? 3 : 2) << k);  // [schedule,] train, Adam per step
+    return DVNR_OK;
+  };
   while (left >= G) {
-    DVNR_CUDA(cudaGraphLaunch(c->exec, s));
-    count_launches((p.sched ? 3 : 2) * G);  // [schedule,] train, Adam per step
+    dvnr_status rc = run_graph(kMaxGraphLog);
+    if (rc != DVNR_OK) return rc;
     left -= G;
   }
+  for (int k = kMaxGraphLog - 1; k >= kMinGraphLog; --k) {
+    if (left >= (1 << k)) {
+      dvnr_status rc = run_graph(k);
+      if (rc != DVNR_OK) return rc;
+      left -= 1 << k;
+    }
+  }
+  count_eager_steps(left);
   for (int64_t i = 0; i < left; ++i) {
     dvnr_status rc = one_step(s);
     if (rc != DVNR_OK) return rc;
@@ -1425,6 +1506,7 @@ dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_m
   }
   p.ghost = m->box.ghost;
   p.out = out;
+  p.first_wait_cycles = g_first_wait.load();
   p.div_e0 = make_fastdiv((uint64_t)p.e[0]);
   p.div_e1 = make_fastdiv((uint64_t)p.e[1]);
   for (int a = 0; a < 3; ++a) p.div_fix[a] = make_fastdiv(2 * (uint64_t)std::max<int64_t>(p.nstore[a] - 1, 1));
@@ -1447,6 +1529,17 @@ dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_m
 }
 
 }  // namespace dvnr
+
+extern "C" dvnr_status dvnr_debug_first_wait(int64_t cycles, int64_t* previous) {
+  using namespace dvnr;
+  if (cycles < -1) {
+    set_error("cycles must be >= 0, or -1 for the default");
+    return DVNR_E_INVALID;
+  }
+  const long long prev = g_first_wait.exchange(cycles == -1 ? kWaitCycles : (long long)cycles);
+  if (previous) *previous = prev;
+  return DVNR_OK;
+}
 
 extern "C" dvnr_status dvnr_selftest_umma(int32_t* mismatches_host) {
   using namespace dvnr;

@@ -54,6 +54,13 @@ void device_counter_free(unsigned long long* p) {
 
 bool profiling_on() { return g_on.load(); }
 void count_launches(int64_t n) { g_launches.fetch_add(n); }
+
+// How the grouped training ran its steps: graphs captured and replayed, and
+// steps launched directly.
+std::atomic<int64_t> g_graph_captures{0}, g_graph_replays{0}, g_eager_steps{0};
+void count_graph_capture() { g_graph_captures.fetch_add(1); }
+void count_graph_replay() { g_graph_replays.fetch_add(1); }
+void count_eager_steps(int64_t n) { g_eager_steps.fetch_add(n); }
 void set_capturing(bool on) { g_capturing = on; }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
@@ -119,6 +126,13 @@ int64_t dvnr_launch_count(void) {
   int64_t n = g_launches.load();
   for (unsigned long long* p : g_dev_counters) n += (int64_t)*reinterpret_cast<volatile unsigned long long*>(p);
   return n;
+}
+
+dvnr_status dvnr_graph_stats(int64_t* captures, int64_t* replays, int64_t* eager_steps) {
+  if (captures) *captures = dvnr::g_graph_captures.load();
+  if (replays) *replays = dvnr::g_graph_replays.load();
+  if (eager_steps) *eager_steps = dvnr::g_eager_steps.load();
+  return DVNR_OK;
 }
 
 }  // extern "C"

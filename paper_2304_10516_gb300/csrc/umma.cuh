@@ -112,12 +112,31 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity
   return ok;
 }
 
+// Non-blocking probe: has the phase with `parity` completed?
+__device__ __forceinline__ uint32_t mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok;
+}
+
 // Bounded wait for the phase with `parity` to complete. Gives up after
 // ~`limit_cycles` SM clocks or when another thread has raised *abort; returns
-// false then (the caller records the timeout and winds down).
+// false then (the caller records the timeout and winds down). A limit <= 0
+// gives up unless the phase is complete at the first, non-blocking probe.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
                                                   volatile uint32_t* abort,
                                                   long long limit_cycles) {
+  if (limit_cycles <= 0) {
+    if (mbar_test_wait(bar, parity)) return true;
+    *abort = 1u;
+    return false;
+  }
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
   const AdamModelPtrs md = models[blockIdx.y];
   ModelState* st = md.st;
   if (h.gated && !model_active(st)) return;  // budget spent or stopped: no work, no counters
-  const bool skip = *((volatile uint32_t*)&st->overflow) != 0u;
+  const uint32_t ov = *((volatile uint32_t*)&st->overflow);
+  const bool skip = ov != 0u;
   const float S = h.mixed ? st->loss_scale : 1.0f;
   const float inv_S = 1.0f / S;
   const uint32_t t = st->adam_t + 1u;
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
       if (skip) {
         st->skipped += 1u;
         st->good_steps = 0u;
-        if (h.mixed) st->loss_scale = S * 0.5f;
+        if (h.mixed && (ov & kNonFiniteGrad)) st->loss_scale = S * 0.5f;
       } else {
         st->adam_t = t;
         if (h.mixed) {
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
         }
       }
       const float L = st->loss_sum * h.inv_batch;
-      st->last_loss = L;
-      if (!skip) {
+      if (!h.external) st->last_loss = L;
+      if (!skip && !h.external) {
         // moving average of the loss over the finite steps of the call and
         // the early-stop test (Sec. 3.2)
         const float e = st->loss_ema < 0.f ? L : __fadd_rn(__fmul_rn(h.stop_decay, st->loss_ema),
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
       }
       st->loss_sum = 0.f;
       st->overflow = 0u;
-      st->iter += 1u;
+      if (!h.external) st->iter += 1u;
       st->done_blocks = 0u;
     }
   }
@@ -275,12 +276,14 @@ __global__ void k_state_reset(ModelState* st, float loss_scale) {
 }
 
 // Start of a training call: the budget runs from the current iteration (the
-// end saturates at 2^32 - 1) and the moving average starts afresh.
+// end saturates at 2^32 - 1), the moving average starts afresh and the
+// timeout count starts at zero (it reports this call's bounded waits).
 __global__ void k_begin_call(ModelState* st, uint32_t budget) {
   const uint32_t it = st->iter;
   st->stop_at = budget > 0xFFFFFFFFu - it ? 0xFFFFFFFFu : it + budget;
   st->loss_ema = -1.f;
   st->stopped = 0u;
+  st->timeouts = 0u;
 }
 
 // Hand out the gradient of one forward/backward without an optimiser step:
@@ -308,6 +311,22 @@ __global__ void k_finish_grad(float* __restrict__ grad, int64_t n_params,
       st->done_blocks = 0u;
     }
   }
+}
+
+// grad[storage j] = g_in[compact i] S (S the loss scale on the FP16 path, else
+// 1); a value that is or becomes non-finite flags the step. Storage padding is
+// never written (it stays zero).
+__global__ void k_load_grad(float* __restrict__ grad, const float* __restrict__ g_in, int64_t n_params,
+                            LayoutMap lmap, ModelState* st, int mixed) {
+  const float S = mixed ? st->loss_scale : 1.0f;
+  bool bad = false;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_params;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float g = g_in[i] * S;
+    bad |= !isfinite(g);
+    grad[ext_to_int(lmap, i)] = g;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->overflow, kNonFiniteGrad);
 }
 
 __global__ void k_state_set_scale(ModelState* st, float loss_scale) {
@@ -342,6 +361,16 @@ dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_ba
     k_finish_grad<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(
       m->grad, m->n_params, m->lmap, 1.0f / loss_scale_used, grad_out, m->st,
       inv_batch, loss_out);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_load_grad(dvnr_model m, const float* grad_in, bool mixed, cudaStream_t s) {
+  {
+    ProfScope ps_("load_grad", s);
+    k_load_grad<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(m->grad, grad_in, m->n_params, m->lmap,
+                                                                     m->st, mixed ? 1 : 0);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;

@@ -245,6 +245,23 @@ class Model:
                _stream(stream))
         return outs
 
+    def adam_step(self, grad, cfg: TrainConfig, stream=None):
+        """One Adam step (Sec. 3.6) from a caller-given gradient: a float32
+        device tensor of n_params values in the compact layout (unscaled)."""
+        import torch
+
+        g = grad.detach().to(torch.float32).contiguous().reshape(-1)
+        assert g.numel() == self.n_params and g.is_cuda
+        c = cfg.to_c()
+        A.call("dvnr_adam_step", self._h, _ptr(g), C.byref(c), _stream(stream))
+
+    def moments(self):
+        """(m1, m2): the Adam moments in the compact layout (host arrays)."""
+        m1 = np.empty(self.n_params, dtype=np.float32)
+        m2 = np.empty(self.n_params, dtype=np.float32)
+        A.call("dvnr_get_moments", self._h, m1.ctypes.data, m2.ctypes.data, self.n_params)
+        return m1, m2
+
     # ------------------------------------------------------------ inference
     def decode_points(self, xyz, stream=None):
         import torch

@@ -87,6 +87,27 @@ def composite_sort_last(rgba, depth: float, stream=None):
     return dv.composite(images, depths, stream=stream)
 
 
+def sort_last_frame(depths, render_depth, composite, gather=None):
+    """The frame of all ranks' partitions, composited sort-last (Sec. 4.3).
+
+    Partitions at one depth (e.g. one z-layer of a box decomposition) cover
+    disjoint pixels, so a rank's partitions at one depth form one image;
+    partitions at different depths must blend in depth order, whichever rank
+    holds them. For every depth of the global decomposition (`depths`, the
+    same list on every rank), each rank renders its own partitions at that
+    depth (`render_depth(d)`, an empty image when it holds none there) and the
+    images of all ranks are gathered (`gather`, default gather_images); then
+    `composite(images, depths)` blends all of them front to back (stable
+    in depth order; images of one depth do not overlap)."""
+    gather = gather or gather_images
+    images, ds = [], []
+    for d in depths:
+        ims, dd = gather(render_depth(d), d)
+        images += ims
+        ds += dd
+    return composite(images, ds)
+
+
 def global_psnr(sse: float, count: int, value_range: float = 1.0):
     """PSNR over the voxels of all ranks (Sec. 5): the squared errors and
     voxel counts are summed over ranks in FP64 first (voxel-weighted)."""

@@ -19,6 +19,7 @@ def test_algorithmic_bytes_per_unit():
 
 
 def test_training_profile_is_of_the_current_kernel_revision():
-    t = bench.measured_traffic("train_fused_fp16", "spectral256")
-    assert t is not None and t > 0, "profiles/k_mp_train_fp16_spectral256.md names another kernel revision"
-    assert bench.measured_traffic("adam", "spectral256") is None
+    t, src = bench.measured_traffic("train_fused_fp16", "spectral256")
+    assert t is not None and t > 0, src
+    assert "profiles/k_mp_train_fp16_spectral256.md" in src and "not this run" in src
+    assert bench.measured_traffic("adam", "spectral256") == (None, None)
