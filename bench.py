@@ -187,17 +187,20 @@ def run_ours(args, rank, world, local_rank):
     model = new_model(100 + rank)
     stream = torch.cuda.current_stream()
     gpu_index = local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0
+    # clocks sampled from the warm-up through the timed region (a 20-step
+    # timed call lasts about 9 ms, shorter than the sampling interval)
+    clocks = ClockSampler(gpu_index)
     # warm-up (untimed): W steps, then one call of the timed step count, which
     # captures the step graphs that count replays (a capture never falls in
     # the timed region)
     dv.train([model], [vol], cfg(max(args.warmup, 3)), sync=True)
     dv.train([model], [vol], cfg(args.steps), sync=True)
+    dv.train([model], [vol], cfg(max(args.steps, 200)), sync=True)  # under load while sampling
     if world > 1:
         import torch.distributed as dist
 
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(gpu_index)
     launches0 = lib.dvnr_launch_count()
     g0 = graph_stats(A)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -221,8 +224,9 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": w["desc"], "global_batch": w["batch"] * world,
                    "parallelism": f"{world} independent partition models (no exchange)",
                    "precision": prec, "l2": "working set > L2 (no flush needed)",
-                   "warmup_extra": f"one untimed call of {args.steps} steps after the warm-up "
-                                   "(captures the step graphs the timed call replays)"},
+                   "warmup_extra": f"after the warm-up, one untimed call of {args.steps} steps "
+                                   "(captures the step graphs the timed call replays) and one of "
+                                   f"{max(args.steps, 200)} steps (load while the clocks are sampled)"},
         "clocks": clk, "gpu_launches": int(launches),
         "graph": {"captures_in_timed_region": g1[0] - g0[0], "graph_launches": g1[1] - g0[1],
                   "eager_steps": g1[2] - g0[2],
@@ -319,19 +323,40 @@ def roofline_leg(A, dv, model, vol, cfg, w, args):
         if cnt.value:
             kern[n] = (tms.value, cnt.value)
     A.call("dvnr_profile_enable", 0)
-    total = sum(v[0] for v in kern.values())
-    dom = max(kern, key=lambda k: kern[k][0])
-    dms, dcnt = kern[dom]
-    byt = kernel_bytes(dom, w, model.n_params, w["batch"])
-    ach = byt / (dms / dcnt / 1e3) / 1e9 if byt else None
-    traffic, src = measured_traffic(dom, args.workload)
-    return {
-        "kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-        "frac": (ach / hbm_peak) if ach else None, "traffic": traffic, "traffic_source": src,
-        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-        "avg_launch_ms": dms / dcnt, "algorithmic_bytes_per_launch": byt,
-        "share": {k: round(v[0] / total, 4) for k, v in kern.items()},
-    }
+    out = _roofline(kern, w, model.n_params, w["batch"], hbm_peak, bool(peaks), nprof)
+    dom = out["kernel"]
+    out["traffic"], out["traffic_source"] = measured_traffic(dom, args.workload)
+    if dom == "train_fused_fp16" and w["F"] == 2:
+        out["request_ceiling"] = request_ceiling(A, model, vol, w, out["kernel_ms_per_step"])
+    return out
+
+
+def request_ceiling(A, model, vol, w, kernel_ms):
+    """The resource that binds the training kernel is the rate of scattered
+    L1/L2 requests, for which no datasheet figure exists: measure it. The
+    library's probe issues the training step's exact requests (samples,
+    volume corners, staged table gathers, gradient reductions) without the
+    MLP at 1 to 8 CTAs of 128 threads per SM; its fastest launch is the
+    ceiling of that request pattern here, and the kernel's time is reported
+    as a fraction of it."""
+    import ctypes as C
+
+    rows = {}
+    for ctas in (1, 2, 3, 4, 6, 8):
+        ms = (C.c_double * 2)()
+        A.call("dvnr_probe_requests", model.handle, vol.data_ptr(), w["batch"], ctas, 7, 10,
+               C.cast(ms, C.c_void_p))
+        rows[str(int(ms[1]))] = ms[0]
+    parts = {}
+    for name, mode in (("gathers", 1), ("reductions", 2), ("volume", 4)):
+        ms = (C.c_double * 2)()
+        A.call("dvnr_probe_requests", model.handle, vol.data_ptr(), w["batch"], 2, mode, 10,
+               C.cast(ms, C.c_void_p))
+        parts[name] = ms[0]
+    best = min(rows.values())
+    return {"probe_ms_by_ctas_per_sm": rows, "best_ms": best, "kernel_ms": kernel_ms,
+            "frac": best / kernel_ms, "parts_ms_at_2_ctas_per_sm": parts,
+            "what": "the training step's memory requests alone (no MLP), fastest launch shape"}
 
 
 def _mean_se(xs):
@@ -426,16 +451,22 @@ def _profile(A, names):
     return out
 
 
-def _roofline(kern, w, n_params, units, hbm_peak, have_peaks):
+def _roofline(kern, w, n_params, units, hbm_peak, have_peaks, steps):
+    """Roofline of the dominant kernel over `steps` profiled steps: its
+    algorithmic bytes per step (per unit x units of a step) over its device
+    time per step. A step is one training launch, or one per wave when the
+    step interleaves Adam wave by wave, so the time is taken per step."""
     total = sum(v[0] for v in kern.values())
     dom = max(kern, key=lambda k: kern[k][0])
     dms, dcnt = kern[dom]
     byt = kernel_bytes(dom, w, n_params, units)
-    ach = byt / (dms / dcnt / 1e3) / 1e9 if byt else None
+    per_step = dms / steps
+    ach = byt / (per_step / 1e3) / 1e9 if byt else None
     return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
             "frac": (ach / hbm_peak) if ach else None, "traffic": None,
             "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if have_peaks else "fallback",
-            "avg_launch_ms": dms / dcnt,
+            "kernel_ms_per_step": per_step, "launches_per_step": dcnt / steps,
+            "avg_launch_ms": dms / dcnt, "algorithmic_bytes_per_step": byt,
             "share": {k: round(v[0] / total, 4) for k, v in kern.items()}}
 
 
@@ -508,15 +539,16 @@ def blocks_measure(args, rank, world, local_rank, compact=False):
                               sigma_bnd=0.005, precision=prec, seed=7)
 
     stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0 if "CUDA_VISIBLE_DEVICES" in os.environ else local_rank)
     # warm-up, then one untimed call of the timed step count (step graphs)
     dv.train(models, vols, cfg(max(args.warmup, 3)))
     dv.train(models, vols, cfg(args.steps))
+    dv.train(models, vols, cfg(max(args.steps, 64)))  # under load while sampling
     if world > 1:
         import torch.distributed as dist
 
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0 if "CUDA_VISIBLE_DEVICES" in os.environ else local_rank)
     l0 = lib.dvnr_launch_count()
     g0 = graph_stats(A)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -540,8 +572,9 @@ def blocks_measure(args, rank, world, local_rank, compact=False):
                    "parallelism": f"64 partition models split over {world} GPU(s) by LPT on voxel "
                                   "count, one grouped launch per step per GPU",
                    "l2": "working set > L2 (no flush needed)",
-                   "warmup_extra": f"one untimed call of {args.steps} steps after the warm-up "
-                                   "(captures the step graphs the timed call replays)"},
+                   "warmup_extra": f"after the warm-up, one untimed call of {args.steps} steps "
+                                   "(captures the step graphs the timed call replays) and one of "
+                                   f"{max(args.steps, 64)} steps (load while the clocks are sampled)"},
         "clocks": clk, "gpu_launches": int(launches),
         "graph": {"captures_in_timed_region": g1[0] - g0[0], "graph_launches": g1[1] - g0[1],
                   "eager_steps": g1[2] - g0[2]}}
@@ -550,10 +583,11 @@ def blocks_measure(args, rank, world, local_rank, compact=False):
     if rank == 0:
         hbm, have = _peaks()
         A.call("dvnr_profile_enable", 1)
-        dv.train(models, vols, cfg(min(args.steps, 20)))
+        nprof = min(args.steps, 20)
+        dv.train(models, vols, cfg(nprof))
         kern = _profile(A, ["train_fused_fp16", "mp_schedule", "adam", "minmax"])
         A.call("dvnr_profile_enable", 0)
-        res["roofline"] = _roofline(kern, w, models[0].n_params * n, n * w["batch"], hbm, have)
+        res["roofline"] = _roofline(kern, w, models[0].n_params * n, n * w["batch"], hbm, have, nprof)
         if args.legs == "roofline" and not compact:  # the roofline leg alone (profiling)
             return res
     # full training from fresh models, then decode and PSNR over owned voxels
@@ -885,7 +919,8 @@ def learned_gain(model, untrained, vol, dv, w, new_model, cfg):
            "psnr_grid_same_bytes": p_grid, "max_abs_grid_same_bytes": mx_grid,
            "grid_side_same_bytes": side}
     curve = []
-    for log2T, steps in ((19, 8000), (18, 2000), (17, 2000), (16, 2000), (16, 8000)):
+    for log2T, steps in ((19, 8000), (18, 2000), (17, 2000), (16, 2000), (16, 8000), (14, 2000),
+                         (12, 2000), (12, 8000)):
         enc = dv.EncodingConfig(w["L"], w["F"], log2T, w["base"], w["growth"])
         m = new_model(100, enc)
         dv.train([m], [vol], cfg(steps), sync=True)

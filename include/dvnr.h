@@ -325,6 +325,41 @@ dvnr_status dvnr_adam_step(dvnr_model m, const float* grad_dev, const dvnr_train
  * may be NULL. Synchronises the device. DVNR_E_STATE for a frozen model.    */
 dvnr_status dvnr_get_moments(dvnr_model m, float* m1_host, float* m2_host, int64_t n);
 
+/* The network as a differentiable function of its parameters (Sec. 3: the
+ * INR is the hash-grid encoding followed by the MLP; Sec. 3.6: trained by
+ * back-propagation through both), for callers that build their own losses
+ * (e.g. a torch.autograd.Function). Coordinates are fixed point, as in
+ * training: coords_dev holds n x 3 uint32 values m in [0, 2^24], u = m 2^-24
+ * in the model's unit domain. precision selects the kernels: DVNR_FP32 the
+ * plain FP32 path (FP32 master weights), DVNR_FP16 the tensor-core path
+ * (the FP16 copy of the weights, the training kernel's rounding points).
+ *
+ * load_params: set the FP32 master weights from params_dev (n_enc + n_mlp
+ *   float32 on the device, compact layout of dvnr_get_weights) and refresh
+ *   the FP16 copy; Adam moments and step counters are kept. Asynchronous.
+ * forward: y_dev[i] = network output at point i, in normalised units (no
+ *   value range applied). Asynchronous.
+ * backward: the gradient of L with respect to every parameter, given
+ *   dy_dev[i] = dL/dy_i (n float32): grad_dev receives n_enc + n_mlp float32
+ *   in the compact layout (tables, then the MLP weights), dx0_dev (may be
+ *   NULL) the n x (n_levels n_features) values dL/d(encoding). The same
+ *   fused training kernel as dvnr_train with the loss replaced by dy and the
+ *   samples by the given points. FP16: dy is multiplied by a loss scale S
+ *   before the backward pass and every gradient divided by it again:
+ *   loss_scale > 0 is used as given, 0 picks S = 2^k with max|dy| S in
+ *   [1, 2) (S = 1 when dy is zero or not finite); FP32 ignores loss_scale.
+ *   Non-finite values propagate into the outputs. Uses the model's gradient
+ *   buffer (zero between calls), so it must not overlap a training call of
+ *   the same model. 1 <= n <= 2^30. Synchronises `stream`.
+ * Errors: DVNR_E_INVALID, DVNR_E_STATE (frozen model; FP32 forward of a
+ * frozen model), DVNR_E_UNSUPPORTED, DVNR_E_CUDA.                            */
+dvnr_status dvnr_load_params(dvnr_model m, const float* params_dev, void* stream);
+dvnr_status dvnr_forward(dvnr_model m, const uint32_t* coords_dev, int64_t n, int32_t precision,
+                         float* y_dev, void* stream);
+dvnr_status dvnr_backward(dvnr_model m, const uint32_t* coords_dev, int64_t n, const float* dy_dev,
+                          int32_t precision, float loss_scale, float* grad_dev, float* dx0_dev,
+                          void* stream);
+
 /* Point inference (Sec. 3, Sec. 4.1): n points in global voxel coordinates
  * (x, y, z float32 triples; voxel centre of global index j is at j) mapped
  * into the model's unit domain, clamped to it, evaluated and de-normalised
@@ -497,6 +532,35 @@ dvnr_status dvnr_graph_stats(int64_t* captures, int64_t* replays, int64_t* eager
  * Process-wide; *previous (may be NULL) receives the limit it replaces.
  * DVNR_E_INVALID for cycles < -1.                                            */
 dvnr_status dvnr_debug_first_wait(int64_t cycles, int64_t* previous);
+
+/* Measurement of the memory-request pattern of one FP16 training step of
+ * model m (the training kernel is bound by scattered L1/L2 requests, not by
+ * DRAM bandwidth or the tensor cores): the same Philox samples (seed 7,
+ * iteration k for the k-th launch), trilinear volume reads of vol_dev (m's
+ * stored block), staged gathers of the FP16 table corners and vector
+ * reductions into a scratch FP32 gradient as the training kernel issues
+ * them for `batch` samples, tile by tile over a persistent grid of 128-thread
+ * CTAs, with no MLP. mode: bit 0 gathers, bit 1 reductions, bit 2 volume
+ * reads. At most ctas_per_sm CTAs run per SM (1..16; fewer when registers or
+ * shared memory do not allow them). One untimed launch, then `iters` timed
+ * with CUDA events: ms_out[0] = mean ms per launch, ms_out[1] = CTAs per SM
+ * that ran. The model is not changed. Needs 2 features per level and at
+ * most 64 encoding values (else DVNR_E_UNSUPPORTED). Synchronises the
+ * device's default stream.                                                  */
+dvnr_status dvnr_probe_requests(dvnr_model m, const float* vol_dev, int32_t batch, int32_t ctas_per_sm,
+                                int32_t mode, int32_t iters, double* ms_out);
+
+/* Diagnostics for tests of the cleanup paths. Every device allocation the
+ * library makes (models, workspaces, graph caches, per-call temporaries)
+ * goes through one counted layer.
+ *  - fail_alloc: the nth device allocation from now fails as if the device
+ *    were out of memory (the call reports DVNR_E_OOM and releases what it
+ *    had allocated); nth = 0 disarms. Process-wide; the countdown is
+ *    consumed by the allocation it reaches. DVNR_E_INVALID for nth < 0.
+ *  - live_allocs: the number and bytes of device allocations the library
+ *    holds now (count and bytes may be NULL).                               */
+dvnr_status dvnr_debug_fail_alloc(int64_t nth);
+dvnr_status dvnr_debug_live_allocs(int64_t* count, int64_t* bytes);
 
 /* Diagnostic of the tensor-core operand layouts used by the FP16 path: one
  * 128 x 64 x 64 tcgen05 product per operand order (A K-major/MN-major x

@@ -32,7 +32,9 @@ EXPORTS = [
     "dvnr_adaptive_encoding", "dvnr_freeze", "dvnr_window_create", "dvnr_window_destroy",
     "dvnr_window_push", "dvnr_window_range", "dvnr_window_model", "dvnr_window_bytes",
     "dvnr_render_in_frame", "dvnr_composite", "dvnr_set_value_range", "dvnr_adam_step",
-    "dvnr_get_moments", "dvnr_debug_first_wait", "dvnr_graph_stats",
+    "dvnr_get_moments", "dvnr_debug_first_wait", "dvnr_graph_stats", "dvnr_load_params",
+    "dvnr_forward", "dvnr_backward", "dvnr_debug_fail_alloc", "dvnr_debug_live_allocs",
+    "dvnr_probe_requests",
 ]
 
 
@@ -130,6 +132,12 @@ _SIGS = {
     "dvnr_get_moments": ([_P, _P, _P, C.c_int64], C.c_int),
     "dvnr_debug_first_wait": ([C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "dvnr_graph_stats": ([C.POINTER(C.c_int64)] * 3, C.c_int),
+    "dvnr_load_params": ([_P, _P, _P], C.c_int),
+    "dvnr_debug_fail_alloc": ([C.c_int64], C.c_int),
+    "dvnr_probe_requests": ([_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P], C.c_int),
+    "dvnr_debug_live_allocs": ([C.POINTER(C.c_int64), C.POINTER(C.c_int64)], C.c_int),
+    "dvnr_forward": ([_P, _P, C.c_int64, C.c_int32, _P, _P], C.c_int),
+    "dvnr_backward": ([_P, _P, C.c_int64, _P, C.c_int32, C.c_float, _P, _P, _P], C.c_int),
     "dvnr_import_fp16": ([_P, _P, C.c_int64], C.c_int),
 }
 

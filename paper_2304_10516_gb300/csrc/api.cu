@@ -188,6 +188,7 @@ AdamHyper adam_hyper(const dvnr_train_cfg* cfg, bool mixed) {
   h.stop_loss = cfg->stop_loss;
   h.stop_decay = cfg->stop_decay;
   h.external = 0;
+  h.dry = 0;
   return h;
 }
 
@@ -292,7 +293,7 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
   const size_t b32 = align256(P * 4), b16 = align256(P * 2), bst = align256(sizeof(ModelState)),
                bq = align256((kQTab + 1) * sizeof(int32_t)), bap = align256(sizeof(AdamModelPtrs));
   m->block_bytes = 4 * b32 + b16 + bst + bq + bap;
-  ce = cudaMalloc(&m->block, m->block_bytes);
+  ce = dev_malloc(reinterpret_cast<void**>(&m->block), m->block_bytes);
   if (ce != cudaSuccess) {
     delete m;
     return cuda_status(ce, "cudaMalloc(model)");
@@ -311,7 +312,7 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
   st0.enc_max = float_to_ordered(1.f);
   st0.loss_scale = 1.f;
   auto cleanup = [&](dvnr_status s) {
-    cudaFree(m->block);
+    dev_free(m->block);
     delete m;
     return s;
   };
@@ -336,9 +337,9 @@ void dvnr_destroy(dvnr_model m) {
   cudaSetDevice(m->device);
   cudaDeviceSynchronize();
   mp_release(m);
-  if (m->ws.base) cudaFree(m->ws.base);
-  if (m->grid_ws) cudaFree(m->grid_ws);
-  cudaFree(m->block);
+  if (m->ws.base) dev_free(m->ws.base);
+  if (m->grid_ws) dev_free(m->grid_ws);
+  dev_free(m->block);
   if (cur >= 0) cudaSetDevice(cur);
   delete m;
 }
@@ -354,7 +355,7 @@ dvnr_status dvnr_freeze(dvnr_model m, void* stream) {
   if ((rc = launch_refresh_half(m, (cudaStream_t)stream)) != DVNR_OK) return rc;
   const size_t b16 = align256((size_t)m->n_store * 2), bst = align256(sizeof(ModelState));
   void* blk = nullptr;
-  DVNR_CUDA(cudaMalloc(&blk, b16 + bst));
+  DVNR_CUDA(dev_malloc(reinterpret_cast<void**>(&blk), b16 + bst));
   char* p = static_cast<char*>(blk);
   cudaError_t e = cudaMemcpyAsync(p, m->theta16, (size_t)m->n_store * 2, cudaMemcpyDeviceToDevice,
                                   (cudaStream_t)stream);
@@ -362,16 +363,16 @@ dvnr_status dvnr_freeze(dvnr_model m, void* stream) {
     e = cudaMemcpyAsync(p + b16, m->st, sizeof(ModelState), cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) {
-    cudaFree(blk);
+    dev_free(blk);
     return cuda_status(e, "dvnr_freeze");
   }
   mp_release(m);
-  if (m->ws.base) cudaFree(m->ws.base);
+  if (m->ws.base) dev_free(m->ws.base);
   m->ws = Fp32Workspace{};
-  if (m->grid_ws) cudaFree(m->grid_ws);
+  if (m->grid_ws) dev_free(m->grid_ws);
   m->grid_ws = nullptr;
   m->grid_ws_elems = 0;
-  cudaFree(m->block);
+  dev_free(m->block);
   m->block = blk;
   m->block_bytes = b16 + bst;
   m->theta = m->m1 = m->m2 = m->grad = nullptr;
@@ -769,6 +770,69 @@ dvnr_status dvnr_adam_step(dvnr_model m, const float* grad_dev, const dvnr_train
   return DVNR_OK;
 }
 
+dvnr_status dvnr_load_params(dvnr_model m, const float* params_dev, void* stream) {
+  if (!m || !params_dev) return fail(DVNR_E_INVALID, "NULL model or parameters");
+  if (m->frozen) return fail(DVNR_E_STATE, "the model is frozen");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  return launch_load_params(m, params_dev, (cudaStream_t)stream);
+}
+
+dvnr_status dvnr_forward(dvnr_model m, const uint32_t* coords_dev, int64_t n, int32_t precision,
+                         float* y_dev, void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_forward");
+  g_err[0] = 0;
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (n < 0) return fail(DVNR_E_INVALID, "n must be >= 0");
+  if (precision != DVNR_FP32 && precision != DVNR_FP16) return fail(DVNR_E_INVALID, "bad precision");
+  if (n == 0) return DVNR_OK;
+  if (!coords_dev || !y_dev) return fail(DVNR_E_INVALID, "NULL buffer");
+  if (precision == DVNR_FP16 && !mp_supported(m))
+    return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
+  if (precision == DVNR_FP32 && m->frozen) return fail(DVNR_E_STATE, "a frozen model keeps FP16 parameters only");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == DVNR_FP16) return mp_forward(m, coords_dev, n, y_dev, s);
+  return fp32_decode_unit(m, coords_dev, nullptr, n, 0, y_dev, s, true);
+}
+
+dvnr_status dvnr_backward(dvnr_model m, const uint32_t* coords_dev, int64_t n, const float* dy_dev,
+                          int32_t precision, float loss_scale, float* grad_dev, float* dx0_dev,
+                          void* stream) {
+  dvnr::ApiRange nvtx_("dvnr_backward");
+  g_err[0] = 0;
+  if (!m) return fail(DVNR_E_INVALID, "model is NULL");
+  if (m->frozen) return fail(DVNR_E_STATE, "the model is frozen");
+  if (n < 1 || n > (1LL << 30)) return fail(DVNR_E_INVALID, "n must be in [1, 2^30]");
+  if (precision != DVNR_FP32 && precision != DVNR_FP16) return fail(DVNR_E_INVALID, "bad precision");
+  if (!coords_dev || !dy_dev || !grad_dev) return fail(DVNR_E_INVALID, "NULL buffer");
+  if (!(loss_scale >= 0.f) || !std::isfinite(loss_scale)) return fail(DVNR_E_INVALID, "loss_scale must be finite and >= 0");
+  const bool mixed = precision == DVNR_FP16;
+  if (mixed && !mp_supported(m))
+    return fail(DVNR_E_UNSUPPORTED, "FP16 path needs n_levels*n_features <= 64, width 16, 32 or 64 and 1, 2, 4 or 8 features per level");
+  dvnr_status rc = use_device(m);
+  if (rc != DVNR_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (mixed) {
+    if ((rc = launch_ext_scale(m, dy_dev, n, loss_scale, s)) != DVNR_OK) return rc;
+    if ((rc = mp_backward(m, coords_dev, dy_dev, n, &m->st->ext_scale, dx0_dev, s)) != DVNR_OK) return rc;
+    return launch_finish_grad_dev(m, &m->st->ext_scale, grad_dev, s);
+  }
+  Fp32StepArgs a{};
+  a.m = m;
+  a.vol = nullptr;
+  a.batch = (int32_t)n;
+  a.loss = DVNR_LOSS_L2;
+  a.explicit_iter = true;
+  a.gated = false;
+  a.dx0_out = dx0_dev;
+  a.ext_coords = coords_dev;
+  a.ext_dy = dy_dev;
+  if ((rc = fp32_forward_backward(a, s)) != DVNR_OK) return rc;
+  return launch_finish_grad(m, 1.0f, 1.0f, grad_dev, nullptr, s);
+}
+
 dvnr_status dvnr_get_moments(dvnr_model m, float* m1_host, float* m2_host, int64_t n) {
   if (!m) return fail(DVNR_E_INVALID, "model is NULL");
   if (m->frozen) return fail(DVNR_E_STATE, "a frozen model keeps no optimiser state");
@@ -847,11 +911,11 @@ static dvnr_status render_grid(const dvnr_model* models, int32_t n, const float 
     if (m->grid_ws_elems < ne) {
       if (m->grid_ws) {
         DVNR_CUDA(cudaStreamSynchronize(s));
-        cudaFree(m->grid_ws);
+        dev_free(m->grid_ws);
         m->grid_ws = nullptr;
         m->grid_ws_elems = 0;
       }
-      DVNR_CUDA(cudaMalloc(&m->grid_ws, ne * sizeof(float)));
+      DVNR_CUDA(dev_malloc(reinterpret_cast<void**>(&m->grid_ws), ne * sizeof(float)));
       m->grid_ws_elems = ne;
     }
     if ((rc = dvnr_decode_grid(m, m->grid_ws, stream)) != DVNR_OK) return rc;
@@ -867,11 +931,12 @@ static dvnr_status render_grid(const dvnr_model* models, int32_t n, const float 
   std::stable_sort(blocks.begin(), blocks.end(),
                    [](const RenderBlock& a, const RenderBlock& b) { return a.lo[2] < b.lo[2]; });
   RenderBlock* dblocks = nullptr;
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dblocks), blocks.size() * sizeof(RenderBlock), s));
-  DVNR_CUDA(cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(RenderBlock),
-                            cudaMemcpyHostToDevice, s));
-  rc = launch_render(dblocks, n, lo, hi, *tf, w, h, spr, rgba_dev, s);
-  cudaFreeAsync(dblocks, s);
+  DVNR_CUDA(dev_malloc_async(reinterpret_cast<void**>(&dblocks), blocks.size() * sizeof(RenderBlock), s));
+  const cudaError_t e = cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(RenderBlock),
+                                        cudaMemcpyHostToDevice, s);
+  rc = e == cudaSuccess ? launch_render(dblocks, n, lo, hi, *tf, w, h, spr, rgba_dev, s)
+                        : cuda_status(e, "dvnr_render");
+  dev_free_async(dblocks, s);
   if (rc == DVNR_OK) DVNR_CUDA(cudaStreamSynchronize(s));  // the host block table is released
   return rc;
 }
@@ -949,14 +1014,14 @@ dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n, 
   if (!out_host || n < 0 || (n > 0 && (!a_dev || !b_dev))) return fail(DVNR_E_INVALID, "bad argument");
   cudaStream_t s = (cudaStream_t)stream;
   double* d = nullptr;
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), 2 * sizeof(double), s));
+  DVNR_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d), 2 * sizeof(double), s));
   dvnr_status rc = launch_error_stats(a_dev, b_dev, n, d, s);
   if (rc == DVNR_OK) {
     cudaError_t e = cudaMemcpyAsync(out_host, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = cuda_status(e, "dvnr_error_stats");
   }
-  cudaFreeAsync(d, s);
+  dev_free_async(d, s);
   return rc;
 }
 

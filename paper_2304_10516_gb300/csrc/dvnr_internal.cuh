@@ -46,6 +46,12 @@ struct ProfScope {
 };
 bool profiling_on();
 void count_launches(int64_t n);
+// Device allocations of the library (alloc.cu): counted, and made to fail on
+// request for tests of the cleanup paths. Freeing nullptr does nothing.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
+cudaError_t dev_free_async(void* p, cudaStream_t s);
 // dvnr_graph_stats counters of the grouped training's step graphs
 void count_graph_capture();
 void count_graph_replay();
@@ -119,6 +125,7 @@ struct ModelState {
   uint32_t stop_at;           // the call ends this model's training at iter == stop_at
   float loss_ema;             // moving average of the loss in this call (< 0: none yet)
   uint32_t stopped;           // the moving average fell below the stop threshold
+  float ext_scale;            // loss scale of the last dvnr_backward (FP16 path)
 };
 
 // A model takes part in a training step while its call's budget lasts and it
@@ -402,6 +409,10 @@ struct AdamHyper {
   // drawn and no loss was taken, so the iteration count, the last loss and
   // its moving average stay as they are
   int32_t external;
+  // launch-shape trials: the memory traffic of a step (read g, theta, m, v;
+  // write theta, m, v, the FP16 copy, a cleared g) with every value written
+  // back unchanged (the gradient cleared) and no counter touched
+  int32_t dry;
 };
 dvnr_status launch_adam(const AdamModelPtrs* models_dev, int n_models, int64_t n_params,
                         const AdamHyper& h, cudaStream_t s);
@@ -421,11 +432,17 @@ struct Fp32StepArgs {
   float* dx0_out;
   float* tgt_out;
   uint32_t* coords_out;
+  // backward at caller-given points (dvnr_backward): fixed-point coordinates
+  // (batch x 3) instead of drawn samples and the upstream dL/dy (batch)
+  // instead of the loss; no volume. nullptr in training.
+  const uint32_t* ext_coords = nullptr;
+  const float* ext_dy = nullptr;
 };
 dvnr_status fp32_ensure_workspace(dvnr_model m, int64_t batch);
 dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s);
+// raw: write the network output y itself instead of y (vmax - vmin) + vmin
 dvnr_status fp32_decode_unit(dvnr_model m, const uint32_t* coords, const float* xyz, int64_t n,
-                             int grid_mode, float* out, cudaStream_t s);
+                             int grid_mode, float* out, cudaStream_t s, bool raw = false);
 
 // Render (render.cu)
 struct RenderBlock {
@@ -451,6 +468,15 @@ dvnr_status composite(const float* const* rgba, const int* order, int n, int64_t
                       cudaStream_t s);
 dvnr_status launch_state_reset(ModelState* st, float loss_scale, cudaStream_t s);
 dvnr_status launch_state_reset_scale(ModelState* st, float loss_scale, cudaStream_t s);
+// S for a backward at given points: loss_scale > 0 is taken as it is, else
+// 2^round(-log2 max|dy|) (1 when dy is all zero or not finite), so that the
+// largest scaled output gradient is about 1 as in training; stored in
+// m->st->ext_scale.
+dvnr_status launch_ext_scale(dvnr_model m, const float* dy, int64_t n, float loss_scale, cudaStream_t s);
+// Master weights from a device array in the compact layout, FP16 copy refreshed.
+dvnr_status launch_load_params(dvnr_model m, const float* params, cudaStream_t s);
+// As launch_finish_grad with the loss scale read from *scale_dev.
+dvnr_status launch_finish_grad_dev(dvnr_model m, const float* scale_dev, float* grad_out, cudaStream_t s);
 dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_batch, float* grad_out,
                                float* loss_out, cudaStream_t s);
 

@@ -80,12 +80,17 @@ __global__ void k_sample_encode(LevelTab lv, const float* __restrict__ theta,
                                 SampleParams sp, const ModelState* __restrict__ st, int32_t batch,
                                 int use_iter, uint32_t iter_arg, float* __restrict__ x0,
                                 float* __restrict__ tgt, uint32_t* __restrict__ coords,
-                                int gated) {
+                                int gated, const uint32_t* __restrict__ ext_coords) {
   if (gated && !model_active(st)) return;  // the model's call is over (budget or early stop)
   const uint32_t iter = use_iter ? iter_arg : st->iter;
   float vmin, inv_range;
   value_range(st, vmin, inv_range);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch; i += gridDim.x * blockDim.x) {
+    if (ext_coords) {  // given points: no sampling, no target
+      const uint3 m = make_uint3(ext_coords[3 * i], ext_coords[3 * i + 1], ext_coords[3 * i + 2]);
+      encode_fp32<F>(lv, theta, m, x0 + (size_t)i * lv.in_dim);
+      continue;
+    }
     const uint3 m = draw_sample(sp, (uint32_t)i, iter);
     coords[3 * i] = m.x;
     coords[3 * i + 1] = m.y;
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(128)
     k_out_loss(const float* __restrict__ hH, const float* __restrict__ wout, int W,
                const float* __restrict__ tgt, int32_t batch, int32_t loss, float inv_B,
                float* __restrict__ dzH, float* __restrict__ gwout, ModelState* st,
-               float* __restrict__ y_out, int gated) {
+               float* __restrict__ y_out, int gated, const float* __restrict__ ext_dy) {
   if (gated && !model_active(st)) return;
   __shared__ float s_g[256];
   __shared__ float s_w[256];
@@ -210,8 +215,10 @@ __global__ void __launch_bounds__(128)
   if (valid) {
     float y = 0.f;
     for (int j = 0; j < W; ++j) y += s_w[j] * h[j];
-    const float d = y - tgt[i];
-    if (loss == DVNR_LOSS_L1) {
+    const float d = ext_dy ? 0.f : y - tgt[i];
+    if (ext_dy) {  // the upstream gradient of given points
+      dy = ext_dy[i];
+    } else if (loss == DVNR_LOSS_L1) {
       lval = fabsf(d);
       dy = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * inv_B;
     } else {
@@ -324,7 +331,7 @@ __global__ void k_decode_encode(LevelTab lv, const float* __restrict__ theta, Co
 
 __global__ void k_decode_out(const float* __restrict__ hH, const float* __restrict__ wout, int W,
                              int64_t count, const ModelState* __restrict__ st,
-                             float* __restrict__ out) {
+                             float* __restrict__ out, int raw) {
   float vmin, inv_range;
   value_range(st, vmin, inv_range);
   const float range = inv_range > 0.f ? ordered_to_float(st->enc_max) - vmin : 0.f;
@@ -333,7 +340,7 @@ __global__ void k_decode_out(const float* __restrict__ hH, const float* __restri
     const float* h = hH + i * W;
     float y = 0.f;
     for (int j = 0; j < W; ++j) y += __ldg(wout + j) * h[j];
-    out[i] = y * range + vmin;
+    out[i] = raw ? y : y * range + vmin;
   }
 }
 
@@ -343,7 +350,7 @@ dvnr_status fp32_ensure_workspace(dvnr_model m, int64_t batch) {
   Fp32Workspace& ws = m->ws;
   if (ws.batch >= batch && ws.base) return DVNR_OK;
   if (ws.base) {
-    cudaFree(ws.base);
+    dev_free(ws.base);
     ws = Fp32Workspace{};
   }
   const int64_t D = m->lv.in_dim, W = m->mlp.width, H = m->mlp.n_hidden;
@@ -351,7 +358,7 @@ dvnr_status fp32_ensure_workspace(dvnr_model m, int64_t batch) {
   const int64_t b_x0 = al(batch * D * 4), b_act = al(H * batch * W * 4), b_dz = al(2 * batch * W * 4),
                 b_dx0 = al(batch * D * 4), b_tgt = al(batch * 4), b_c = al(batch * 12);
   void* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, b_x0 + b_act + b_dz + b_dx0 + b_tgt + b_c);
+  cudaError_t e = dev_malloc(reinterpret_cast<void**>(&base), b_x0 + b_act + b_dz + b_dx0 + b_tgt + b_c);
   if (e != cudaSuccess) {
     cudaGetLastError();
     set_error("FP32 workspace allocation failed (%s)", cudaGetErrorString(e));
@@ -377,7 +384,9 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   const int B = a.batch, D = m->lv.in_dim, W = m->mlp.width, H = m->mlp.n_hidden;
   const int nx = (int)m->dims[0], ny = (int)m->dims[1], nz = (int)m->dims[2];
   const int enc_blocks = std::min((B + 127) / 128, 152 * 16);
+  // the scatter reads the points back: drawn ones from coords, given ones in place
   uint32_t* coords = a.coords_out ? a.coords_out : ws.coords;
+  const uint32_t* scatter_coords = a.ext_coords ? a.ext_coords : coords;
   const ModelState* gate = a.gated ? m->st : nullptr;
   {
   ProfScope ps_("fp32_sample_encode", s);
@@ -386,7 +395,8 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   case F:                                                                                        \
     k_sample_encode<F><<<enc_blocks, 128, 0, s>>>(m->lv, m->theta, a.vol, nx, ny, nz, a.sp,     \
                                                   m->st, B, a.explicit_iter ? 1 : 0, a.iter,    \
-                                                  ws.x0, ws.tgt, coords, a.gated ? 1 : 0);      \
+                                                  ws.x0, ws.tgt, coords, a.gated ? 1 : 0,       \
+                                                  a.ext_coords);                                \
     break;
     DVNR_SE(1) DVNR_SE(2) DVNR_SE(4) DVNR_SE(8)
 #undef DVNR_SE
@@ -395,7 +405,8 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   }
   }
   DVNR_CUDA(cudaGetLastError());
-  if (a.tgt_out) DVNR_CUDA(cudaMemcpyAsync(a.tgt_out, ws.tgt, (size_t)B * 4, cudaMemcpyDeviceToDevice, s));
+  if (a.tgt_out && !a.ext_coords)
+    DVNR_CUDA(cudaMemcpyAsync(a.tgt_out, ws.tgt, (size_t)B * 4, cudaMemcpyDeviceToDevice, s));
   // forward: H_{k+1} = ReLU(H_k W_k^T)
   const float* in = ws.x0;
   int in_dim = D;
@@ -415,7 +426,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   ProfScope ps_("fp32_out_loss", s);
   k_out_loss<<<(B + 127) / 128, 128, 0, s>>>(hH, m->theta + m->w_off[H], W, ws.tgt, B, a.loss,
                                              1.0f / (float)B, dz, m->grad + m->w_off[H], m->st,
-                                             a.y_out, a.gated ? 1 : 0);
+                                             a.y_out, a.gated ? 1 : 0, a.ext_dy);
   }
   DVNR_CUDA(cudaGetLastError());
   const int splits = std::max(1, std::min(1024, B / 1024));
@@ -441,7 +452,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
   switch (m->lv.F) {
 #define DVNR_SC(F)                                                                               \
   case F:                                                                                        \
-    k_scatter<F><<<enc_blocks, 128, 0, s>>>(m->lv, coords, ws.dx0, B, m->grad, m->st,          \
+    k_scatter<F><<<enc_blocks, 128, 0, s>>>(m->lv, scatter_coords, ws.dx0, B, m->grad, m->st,  \
                                             a.dx0_out, a.gated ? 1 : 0);                         \
     break;
     DVNR_SC(1) DVNR_SC(2) DVNR_SC(4) DVNR_SC(8)
@@ -453,7 +464,7 @@ dvnr_status fp32_forward_backward(const Fp32StepArgs& a, cudaStream_t s) {
 }
 
 dvnr_status fp32_decode_unit(dvnr_model m, const uint32_t* coords, const float* xyz, int64_t n,
-                             int grid_mode, float* out, cudaStream_t s) {
+                             int grid_mode, float* out, cudaStream_t s, bool raw) {
   if (n <= 0) return DVNR_OK;
   const int D = m->lv.in_dim, W = m->mlp.width, H = m->mlp.n_hidden;
   const int64_t chunk = std::min<int64_t>(n, 1 << 19);
@@ -499,7 +510,8 @@ dvnr_status fp32_decode_unit(dvnr_model m, const uint32_t* coords, const float* 
     }
     {
       ProfScope ps_("fp32_decode_out", s);
-      k_decode_out<<<blocks, 128, 0, s>>>(in, m->theta + m->w_off[H], W, cnt, m->st, out + first);
+      k_decode_out<<<blocks, 128, 0, s>>>(in, m->theta + m->w_off[H], W, cnt, m->st, out + first,
+                                          raw ? 1 : 0);
     }
     DVNR_CUDA(cudaGetLastError());
   }

@@ -330,6 +330,72 @@ __device__ __forceinline__ void encode_to_tile_staged(const LevelTab& lv, const 
   }
 }
 
+// One 16-column chunk of dL/d(encoding) (levels c/F .. c/F + 16/F - 1); with
+// GUARD, levels at or past L (the zero padding of the last chunk) are skipped.
+template <int F, bool GUARD>
+__device__ __forceinline__ bool scatter_chunk(const LevelTab& lv, float* __restrict__ grad, uint3 m,
+                                              const float (&d)[16], int c) {
+  bool bad = false;
+  constexpr int LPC = 16 / F;  // levels per 16-column chunk
+#pragma unroll
+  for (int q = 0; q < LPC; ++q) {
+    const int l = c / F + q;
+    if (GUARD && l >= lv.L) break;
+    uint32_t bx, by, bz;
+    float fx, fy, fz;
+    lattice(m.x, lv.N[l], bx, fx);
+    lattice(m.y, lv.N[l], by, fy);
+    lattice(m.z, lv.N[l], bz, fz);
+    float* tab = grad + lv.off[l];
+#pragma unroll
+    for (int f = 0; f < F; ++f) bad |= !isfinite(d[q * F + f]);
+    if constexpr (F <= 2) {
+      // x-neighbour corners whose entries form an aligned pair {2j, 2j+1}
+      // go out as one vector reduction of both entries
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t y = by + (r & 1), z = bz + (r >> 1);
+        const float wyz = ((r & 1) ? fy : 1.f - fy) * ((r >> 1) ? fz : 1.f - fz);
+        const float w0 = (1.f - fx) * wyz, w1 = fx * wyz;
+        const uint32_t i0 = corner_index(lv, l, bx, y, z);
+        const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
+        if (i1 == (i0 ^ 1u)) {
+          float g[2 * F];
+          const bool odd = (i0 & 1u) != 0u;
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            g[f] = (odd ? w1 : w0) * d[q * F + f];
+            g[F + f] = (odd ? w0 : w1) * d[q * F + f];
+          }
+          red_add<2 * F>(tab + (size_t)(i0 & ~1u) * F, g);
+        } else {
+          float g0[F], g1[F];
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            g0[f] = w0 * d[q * F + f];
+            g1[f] = w1 * d[q * F + f];
+          }
+          red_add<F>(tab + (size_t)i0 * F, g0);
+          red_add<F>(tab + (size_t)i1 * F, g1);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
+                        (((k >> 2) & 1) ? fz : 1.f - fz);
+        const uint32_t idx =
+            corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
+        float g[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) g[f] = w * d[q * F + f];
+        red_add<F>(tab + (size_t)idx * F, g);
+      }
+    }
+  }
+  return bad;
+}
+
 // Backward of the encoding: dL/d(encoding) is read from TMEM (16 columns
 // at a time, the warp-collective load runs on every lane) and each level's
 // gradient times the trilinear weights is added to its 8 corner entries

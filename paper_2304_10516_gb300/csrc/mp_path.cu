@@ -62,7 +62,7 @@ std::atomic<long long> g_first_wait{kWaitCycles};
 
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
-[[maybe_unused]] constexpr int kTrainKernelRevision = 10;
+[[maybe_unused]] constexpr int kTrainKernelRevision = 11;
 
 struct MpModel {
   const __half* theta16;
@@ -95,6 +95,10 @@ struct MpParams {
   // its share of wave 0, then of wave 1, ..., so that the tables and
   // gradients in use at any time stay within L2; a wave may split a model
   int64_t wave_tiles;
+  // the launch trains waves [wave_first, wave_end) of the step (wave_end < 0:
+  // to the last); a step run wave by wave interleaves the Adam updates of
+  // the models each wave begins (see mp_train)
+  int32_t wave_first, wave_end;
   // models of the step: sched[0] = n_active, sched[1 + a] = index of the
   // a-th active model, sched[1 + n_models + m] = position of model m (-1 when
   // inactive), written by k_mp_schedule; nullptr = all n_models take part
@@ -103,6 +107,13 @@ struct MpParams {
   // limit of each CTA's first tensor-core wait (SM clocks; <= 0: give up
   // unless complete at once); later waits use kWaitCycles
   long long first_wait_cycles;
+  // backward at caller-given points (dvnr_backward; single model, no volume):
+  // fixed-point coordinates (batch x 3) instead of drawn samples, the
+  // upstream dL/dy (batch) instead of the loss, and the loss scale read from
+  // *ext_scale; all nullptr in training
+  const uint32_t* ext_coords;
+  const float* ext_dy;
+  const float* ext_scale;
 };
 
 struct MpDecodeParams {
@@ -114,7 +125,11 @@ struct MpDecodeParams {
   const ModelState* st;
   int64_t n, n_tiles;
   const float* xyz;
-  int grid_mode;  // 0: xyz points, 1: the owned grid, 2: ray lattice (depth-major)
+  const uint32_t* coords;  // grid_mode 3: fixed-point coordinates, n x 3
+  // 0: xyz points, 1: the owned grid, 2: ray lattice (depth-major), 3: given
+  // fixed-point coordinates, the network output written without
+  // de-normalisation (dvnr_forward)
+  int grid_mode;
   int64_t e[3], nstore[3];
   RayFrame rf;     // grid_mode 2: the samples of rays r0 .. r0+nr-1 of block rb,
   RayBlock rb;     // point i = sample k0 + i / nr of ray r0 + i % nr
@@ -127,72 +142,6 @@ struct MpDecodeParams {
   FastDiv div_e0, div_e1, div_fix[3], div_nr, div_npx;
   long long first_wait_cycles;  // as MpParams
 };
-
-// One 16-column chunk of dL/d(encoding) (levels c/F .. c/F + 16/F - 1); with
-// GUARD, levels at or past L (the zero padding of the last chunk) are skipped.
-template <int F, bool GUARD>
-__device__ __forceinline__ bool scatter_chunk(const LevelTab& lv, float* __restrict__ grad, uint3 m,
-                                              const float (&d)[16], int c) {
-  bool bad = false;
-  constexpr int LPC = 16 / F;  // levels per 16-column chunk
-#pragma unroll
-  for (int q = 0; q < LPC; ++q) {
-    const int l = c / F + q;
-    if (GUARD && l >= lv.L) break;
-    uint32_t bx, by, bz;
-    float fx, fy, fz;
-    lattice(m.x, lv.N[l], bx, fx);
-    lattice(m.y, lv.N[l], by, fy);
-    lattice(m.z, lv.N[l], bz, fz);
-    float* tab = grad + lv.off[l];
-#pragma unroll
-    for (int f = 0; f < F; ++f) bad |= !isfinite(d[q * F + f]);
-    if constexpr (F <= 2) {
-      // x-neighbour corners whose entries form an aligned pair {2j, 2j+1}
-      // go out as one vector reduction of both entries
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const uint32_t y = by + (r & 1), z = bz + (r >> 1);
-        const float wyz = ((r & 1) ? fy : 1.f - fy) * ((r >> 1) ? fz : 1.f - fz);
-        const float w0 = (1.f - fx) * wyz, w1 = fx * wyz;
-        const uint32_t i0 = corner_index(lv, l, bx, y, z);
-        const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
-        if (i1 == (i0 ^ 1u)) {
-          float g[2 * F];
-          const bool odd = (i0 & 1u) != 0u;
-#pragma unroll
-          for (int f = 0; f < F; ++f) {
-            g[f] = (odd ? w1 : w0) * d[q * F + f];
-            g[F + f] = (odd ? w0 : w1) * d[q * F + f];
-          }
-          red_add<2 * F>(tab + (size_t)(i0 & ~1u) * F, g);
-        } else {
-          float g0[F], g1[F];
-#pragma unroll
-          for (int f = 0; f < F; ++f) {
-            g0[f] = w0 * d[q * F + f];
-            g1[f] = w1 * d[q * F + f];
-          }
-          red_add<F>(tab + (size_t)i0 * F, g0);
-          red_add<F>(tab + (size_t)i1 * F, g1);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
-                        (((k >> 2) & 1) ? fz : 1.f - fz);
-        const uint32_t idx =
-            corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
-        float g[F];
-#pragma unroll
-        for (int f = 0; f < F; ++f) g[f] = w * d[q * F + f];
-        red_add<F>(tab + (size_t)idx * F, g);
-      }
-    }
-  }
-  return bad;
-}
 
 template <int F>
 __device__ __forceinline__ bool scatter_from_tmem(const LevelTab& lv, float* __restrict__ grad,
@@ -342,7 +291,8 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
 
   // tiles are numbered over the active models in order (position a covers
   // tiles [a tpm, (a + 1) tpm)); the waves split that sequence
-  for (int wv = 0; wv < n_waves; ++wv) {
+  const int wv_end = p.wave_end < 0 ? n_waves : min(p.wave_end, n_waves);
+  for (int wv = p.wave_first; wv < wv_end; ++wv) {
   const int64_t wb = (int64_t)wv * p.wave_tiles;
   const int64_t Tw = p.wave_tiles < T_act - wb ? p.wave_tiles : T_act - wb;
   const int64_t g_begin = wb + (Tw * blockIdx.x) / gridDim.x;
@@ -357,7 +307,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
       md = p.models[model];
       sp.model = md.slot;
       iter = p.explicit_iter ? p.iter : md.st->iter;
-      S = p.loss_scale_override > 0.f ? p.loss_scale_override : md.st->loss_scale;
+      S = p.ext_scale ? *p.ext_scale : (p.loss_scale_override > 0.f ? p.loss_scale_override : md.st->loss_scale);
       value_range(md.st, vmin, inv_range);
 #pragma unroll
       for (int j = 0; j < NOUT; ++j) acc_out[j] = 0.f;
@@ -368,9 +318,12 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     // -- sample, target, encode
     const int i = tile * kTile + tid;
     const bool valid = i < p.batch;
-    const uint3 mc = valid ? draw_sample(sp, (uint32_t)i, iter) : make_uint3(0u, 0u, 0u);
+    uint3 mc = make_uint3(0u, 0u, 0u);
+    if (valid)
+      mc = p.ext_coords ? make_uint3(p.ext_coords[3 * i], p.ext_coords[3 * i + 1], p.ext_coords[3 * i + 2])
+                        : draw_sample(sp, (uint32_t)i, iter);
     VolCorners vc{};
-    if (valid) vc = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc);  // in flight during the encode
+    if (valid && md.vol) vc = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc);  // in flight during the encode
 #if DVNR_TRAIN_STAGED
     if constexpr (F == 2) {
       // all gathers of the tile in flight at once, staged in the dZ tile and
@@ -380,7 +333,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     } else
 #endif
       encode_to_tile<F, DVNR_TRAIN_PAIR>(p.lv, md.theta16, mc, valid, s_act, (uint32_t)tid);
-    const float target = valid ? (vol_interp(vc) - vmin) * inv_range : 0.f;
+    const float target = (valid && md.vol) ? (vol_interp(vc) - vmin) * inv_range : 0.f;
     umma::fence_proxy_async();
     umma::fence_before_sync();
     __syncthreads();
@@ -436,7 +389,10 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
 #pragma unroll
       for (int j = 0; j < W; ++j) y += h[j] * s_wout[j];
       float dy = 0.f;
-      if (valid) {
+      if (valid && p.ext_dy) {
+        dy = p.ext_dy[i] * S;
+        if (!isfinite(y)) atomicOr(&md.st->overflow, 1u);
+      } else if (valid) {
         const float d = y - target;
         if (p.loss == DVNR_LOSS_L1) {
           loss_acc += fabsf(d);
@@ -705,6 +661,8 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
         m = make_uint3(dec_unit_to_fixed(frame_x(p.rf, px), p.rb.origin[0], p.rb.nstore[0]),
                        dec_unit_to_fixed(frame_y(p.rf, py), p.rb.origin[1], p.rb.nstore[1]),
                        dec_unit_to_fixed(frame_z(p.rf, p.rb.k0 + (int)k), p.rb.origin[2], p.rb.nstore[2]));
+      } else if (p.grid_mode == 3) {
+        m = make_uint3(p.coords[3 * i], p.coords[3 * i + 1], p.coords[3 * i + 2]);
       } else if (p.grid_mode) {
         const uint64_t q1 = fdiv((uint64_t)i, p.div_e0), q2 = fdiv(q1, p.div_e1);
         const uint64_t x = (uint64_t)i - q1 * (uint64_t)p.e[0], y = q1 - q2 * (uint64_t)p.e[1], z = q2;
@@ -774,7 +732,7 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
       umma::fence_before_sync();
       __syncthreads();
     }
-    if (valid) p.out[i] = y * range + vmin;
+    if (valid) p.out[i] = p.grid_mode == 3 ? y : y * range + vmin;
   }
 teardown:
   if (*abort_flag && tid == 0) {
@@ -945,6 +903,7 @@ struct MpCache {
   int64_t wave_tiles = 0;
   int ctas_per_sm = 0;
   bool scheduled = false;  // the captured graph launches k_mp_schedule
+  bool interleaved = false;  // the captured steps interleave Adam per wave
   // early-stop graph: arm node -> WHILE { steps, k_mp_continue }
   bool looped = false;          // exec holds the loop graph
   bool loop_unavailable = false;  // building it failed once: fixed graphs only
@@ -987,9 +946,9 @@ struct MpCache {
     device_counter_free(arm_launches);
     arm_launches = nullptr;
     arm_launches_dev = nullptr;
-    if (d_models) cudaFree(d_models);
-    if (d_adam) cudaFree(d_adam);
-    if (d_sched) cudaFree(d_sched);
+    if (d_models) dev_free(d_models);
+    if (d_adam) dev_free(d_adam);
+    if (d_sched) dev_free(d_sched);
     if (cap) cudaStreamDestroy(cap);
     d_models = nullptr;
     d_adam = nullptr;
@@ -1025,6 +984,8 @@ MpParams base_params(const dvnr_model m, const MpLayout& lay, const dvnr_train_c
   p.qtab = m->qtab;
   p.inv_batch = 1.0f / (float)cfg->batch;
   p.first_wait_cycles = g_first_wait.load();
+  p.wave_first = 0;
+  p.wave_end = -1;
   return p;
 }
 
@@ -1083,17 +1044,64 @@ dvnr_status launch_train(const MpParams& p, int W, int F, int n_models, cudaStre
   return DVNR_OK;
 }
 
-// Launch-shape autotuner of the grouped training kernel: on the first call
-// for a configuration (encoding, MLP, batch, number of models) it times the
-// fused kernel for each candidate -- CTAs per SM (as many
-// as fit, or one) and models per wave (the heuristic, half, double) -- on the
-// call's own models and volumes, then clears what those trial runs wrote
-// (weight gradients, loss sums, overflow flags; parameters, moments and step
-// counters are not touched) and caches the fastest choice for the process.
-// DVNR_AUTOTUNE=0 keeps the heuristic; DVNR_WAVE_MODELS fixes the wave size.
+// A step run wave by wave ("interleaved"): before the training launch of
+// each wave, the Adam update of the models whose first tile lies in that
+// wave (from the previous step's gradients), so that the FP16 tables the
+// update writes and the gradients it clears are still in L2 when the wave
+// gathers and scatters into them. Each model is updated before any of its
+// tiles trains (launch order), and after all tiles of the previous step;
+// the first step of a call trains without an update and the call ends with
+// one update of every model, so the sequence of operations per model is that
+// of the plain step (train, then Adam). Used when every model takes part in
+// every step (no schedule).
+dvnr_status launch_interleaved_step(const MpParams& q, int W, int F, int n, const AdamModelPtrs* d_adam,
+                                    int64_t n_store, const AdamHyper& h, cudaStream_t s) {
+  const int64_t T = q.total_tiles, wt = q.wave_tiles, tpm = q.tiles_per_model;
+  const int n_waves = (int)((T + wt - 1) / wt);
+  for (int w = 0; w < n_waves; ++w) {
+    const int64_t t0 = (int64_t)w * wt, t1 = std::min(T, t0 + wt);
+    const int m0 = (int)((t0 + tpm - 1) / tpm), m1 = (int)std::min<int64_t>(n, (t1 + tpm - 1) / tpm);
+    if (m1 > m0) {
+      dvnr_status rc = launch_adam(d_adam + m0, m1 - m0, n_store, h, s);
+      if (rc != DVNR_OK) return rc;
+    }
+    MpParams pw = q;
+    pw.wave_first = w;
+    pw.wave_end = w + 1;
+    dvnr_status rc = launch_train(pw, W, F, n, s);
+    if (rc != DVNR_OK) return rc;
+  }
+  return DVNR_OK;
+}
+
+// Kernel launches of one interleaved step (for the launch count).
+int64_t interleaved_launches(const MpParams& q, int n) {
+  const int64_t T = q.total_tiles, wt = q.wave_tiles, tpm = q.tiles_per_model;
+  const int n_waves = (int)((T + wt - 1) / wt);
+  int64_t c = 0;
+  for (int w = 0; w < n_waves; ++w) {
+    const int64_t t0 = (int64_t)w * wt, t1 = std::min(T, t0 + wt);
+    const int m0 = (int)((t0 + tpm - 1) / tpm), m1 = (int)std::min<int64_t>(n, (t1 + tpm - 1) / tpm);
+    c += 1 + (m1 > m0 ? 1 : 0);
+  }
+  return c;
+}
+
+// Launch-shape autotuner of the grouped training step: on the first call
+// for a configuration (encoding, MLP, batch, number of models) it times a
+// whole step for each candidate -- CTAs per SM (as many as fit, or one),
+// models per wave (the heuristic, half, double) or grid rounds per wave,
+// and the step's layout (training launch then Adam, or interleaved per wave
+// when no schedule is needed) -- on the call's own models and volumes, with
+// Adam in its dry mode (the same traffic, values written back unchanged),
+// then clears what the trials wrote (weight gradients, loss sums, overflow
+// flags; parameters, moments and step counters are not touched) and caches
+// the fastest choice for the process. DVNR_AUTOTUNE=0 keeps the heuristic;
+// DVNR_WAVE_MODELS fixes the wave size; DVNR_INTERLEAVE=0/1 fixes the layout.
 struct TuneChoice {
   int ctas_per_sm;
   int64_t wave_tiles;
+  bool interleaved;
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune;
@@ -1106,10 +1114,9 @@ std::string tune_key(const dvnr_model m, int n, const dvnr_train_cfg* cfg) {
   return buf;
 }
 
-dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, TuneChoice* out,
-                     cudaStream_t s) {
+dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, const AdamModelPtrs* d_adam,
+                     const AdamHyper& h, int interleave_env, TuneChoice* out, cudaStream_t s) {
   std::vector<TuneChoice> cands;
-  const int h = heuristic_models_per_wave(base, models[0], n);
   for (int ctas = base.lay.ctas_per_sm; ctas >= 1; ctas = ctas > 1 ? 1 : 0) {
     MpParams q = base;
     q.lay.ctas_per_sm = ctas;
@@ -1119,11 +1126,25 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, Tun
       wt = std::max<int64_t>(1, std::min(wt, T));
       bool dup = false;
       for (const auto& c : cands) dup |= c.ctas_per_sm == ctas && c.wave_tiles == wt;
-      if (!dup) cands.push_back({ctas, wt});
+      if (dup) continue;
+      for (int il = 0; il < 2; ++il) {
+        if (il && base.sched) continue;  // interleaving needs every model in every step
+        if (interleave_env >= 0 && il != interleave_env) continue;
+        cands.push_back({ctas, wt, il != 0});
+      }
     }
     if (ctas == 1) break;
   }
-  (void)h;
+  if (cands.empty()) cands.push_back({base.lay.ctas_per_sm, base.total_tiles, false});
+  AdamHyper hd = h;
+  hd.dry = 1;
+  const int64_t n_store = models[0]->n_store;
+  auto step = [&](const MpParams& q, bool il) -> dvnr_status {
+    if (il) return launch_interleaved_step(q, W, F, n, d_adam, n_store, hd, s);
+    dvnr_status rc = launch_train(q, W, F, n, s);
+    if (rc != DVNR_OK) return rc;
+    return launch_adam(d_adam, n, n_store, hd, s);
+  };
   cudaEvent_t e0, e1;
   DVNR_CUDA(cudaEventCreate(&e0));
   DVNR_CUDA(cudaEventCreate(&e1));
@@ -1134,9 +1155,9 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, Tun
     MpParams q = base;
     q.lay.ctas_per_sm = c.ctas_per_sm;
     set_wave_tiles(q, c.wave_tiles);
-    if ((rc = launch_train(q, W, F, n, s)) != DVNR_OK) break;  // warm-up
+    if ((rc = step(q, c.interleaved)) != DVNR_OK) break;  // warm-up
     cudaEventRecord(e0, s);
-    for (int r = 0; r < 3 && rc == DVNR_OK; ++r) rc = launch_train(q, W, F, n, s);
+    for (int r = 0; r < 3 && rc == DVNR_OK; ++r) rc = step(q, c.interleaved);
     cudaEventRecord(e1, s);
     if (rc != DVNR_OK) break;
     if (cudaEventSynchronize(e1) != cudaSuccess) {
@@ -1233,120 +1254,13 @@ dvnr_status build_loop_graph(MpCache* c, const MpModel* models, int n, int32_t* 
   return DVNR_OK;
 }
 
-}  // namespace
-
-bool mp_supported(const dvnr_model m) {
-  const int D = m->lv.in_dim, W = m->mlp.width, F = m->lv.F;
-  if (!(W == 16 || W == 32 || W == 64)) return false;
-  if (!(F == 1 || F == 2 || F == 4 || F == 8)) return false;
-  if (D < 1 || D > 64) return false;  // padded with zeros to a multiple of 16 for layer 0
-  MpLayout lay;
-  return make_layout(m, true, lay) && make_layout(m, false, lay);
-}
-
-void mp_release(dvnr_model m) {
-  if (m->mp) {
-    MpCache* c = static_cast<MpCache*>(m->mp);
-    c->clear();
-    delete c;
-    m->mp = nullptr;
-  }
-}
-
-dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const uint32_t* slots,
-                     const dvnr_train_cfg* cfg, const AdamHyper& h, int64_t steps, bool uniform,
-                     cudaStream_t s) {
-  dvnr_model m0 = models[0];
-  MpLayout lay;
-  if (!make_layout(m0, true, lay)) {
-    set_error("FP16 path: configuration exceeds shared or tensor memory");
-    return DVNR_E_UNSUPPORTED;
-  }
-  if (!m0->mp) m0->mp = new MpCache();
-  MpCache* c = static_cast<MpCache*>(m0->mp);
-  bool hit = c->d_models && (int)c->uids.size() == n && same_cfg(c->cfg, *cfg);
-  for (int i = 0; hit && i < n; ++i)
-    hit = c->uids[i] == models[i]->uid && c->vols[i] == vols[i] && c->slots[i] == slots[i];
-  if (!hit) {
-    if (c->d_models) DVNR_CUDA(cudaStreamSynchronize(s));
-    c->clear();
-    std::vector<MpModel> hm((size_t)n);
-    std::vector<AdamModelPtrs> ha((size_t)n);
-    for (int i = 0; i < n; ++i) {
-      dvnr_model m = models[i];
-      hm[i] = MpModel{m->theta16, m->grad, vols[i], (int32_t)m->dims[0], (int32_t)m->dims[1],
-                      (int32_t)m->dims[2], slots[i], m->st};
-      ha[i] = AdamModelPtrs{m->theta, m->m1, m->m2, m->grad, m->theta16, m->st};
-    }
-    DVNR_CUDA(cudaMalloc(&c->d_models, sizeof(MpModel) * n));
-    DVNR_CUDA(cudaMalloc(&c->d_adam, sizeof(AdamModelPtrs) * n));
-    DVNR_CUDA(cudaMalloc(&c->d_sched, sizeof(int32_t) * (2 + 2 * (size_t)n)));
-    DVNR_CUDA(cudaMemcpy(c->d_models, hm.data(), sizeof(MpModel) * n, cudaMemcpyHostToDevice));
-    DVNR_CUDA(cudaMemcpy(c->d_adam, ha.data(), sizeof(AdamModelPtrs) * n, cudaMemcpyHostToDevice));
-    c->uids.resize((size_t)n);
-    for (int i = 0; i < n; ++i) c->uids[i] = models[i]->uid;
-    c->vols.assign(vols, vols + n);
-    c->slots.assign(slots, slots + n);
-    c->cfg = *cfg;
-  }
-  MpParams p = base_params(m0, lay, cfg);
-  p.total_tiles = (int64_t)p.tiles_per_model * n;
-  p.n_models = n;
-  // equal budgets and no stop rule: every model takes part in every step, so
-  // the schedule is the identity and its kernel is left out
-  p.sched = (uniform && cfg->stop_loss == 0.f) ? nullptr : c->d_sched;
-  if (p.total_tiles * (int64_t)train_grid(p) >= (1LL << 32)) {
-    set_error("FP16 path: %lld tiles per step is beyond the supported range", (long long)p.total_tiles);
-    return DVNR_E_UNSUPPORTED;
-  }
-  p.models = c->d_models;
-  {
-    const char* at = getenv("DVNR_AUTOTUNE");
-    const bool tune = !(at && atoi(at) == 0) && !getenv("DVNR_WAVE_MODELS") && !getenv("DVNR_WAVE_TILES") &&
-                      !profiling_on() && p.first_wait_cycles == kWaitCycles;
-    const std::string key = tune_key(m0, n, cfg);
-    TuneChoice ch{0, 0};
-    bool have = false;
-    if (tune) {
-      std::lock_guard<std::mutex> lk(g_tune_mu);
-      auto it = g_tune.find(key);
-      if (it != g_tune.end()) {
-        ch = it->second;
-        have = true;
-      }
-    }
-    if (tune && !have) {
-      const int W0 = m0->mlp.width, F0 = m0->lv.F;
-      DVNR_WF_DISPATCH(W0, F0, set_smem_attr, true, lay.smem_bytes);
-      dvnr_status rc = autotune(p, models, n, W0, F0, &ch, s);
-      if (rc != DVNR_OK) return rc;
-      std::lock_guard<std::mutex> lk(g_tune_mu);
-      g_tune[key] = ch;
-      have = true;
-    }
-    if (have) {
-      p.lay.ctas_per_sm = ch.ctas_per_sm;
-      set_wave_tiles(p, ch.wave_tiles);
-    } else {
-      set_waves(p, m0, n);
-    }
-  }
-  if (c->any_graph() && (c->wave_tiles != p.wave_tiles || c->ctas_per_sm != p.lay.ctas_per_sm ||
-                  c->scheduled != (p.sched != nullptr))) {
-    DVNR_CUDA(cudaStreamSynchronize(s));
-    c->drop_graph();
-  }
-  c->wave_tiles = p.wave_tiles;
-  c->ctas_per_sm = p.lay.ctas_per_sm;
-  c->scheduled = p.sched != nullptr;
-  const int W = m0->mlp.width, F = m0->lv.F;
-  DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
-  auto one_step = [&](cudaStream_t st) -> dvnr_status {
-    dvnr_status rc = launch_train(p, W, F, n, st);
-    if (rc != DVNR_OK) return rc;
-    return launch_adam(c->d_adam, n, m0->n_store, h, st);
-  };
-  int64_t left = steps;
+// `left` steps of a grouped call: directly while profiling or a lowered wait
+// limit is active; else the early-stop loop graph when the call has a
+// schedule, or the fixed graphs of 2^k steps (binary digits of `left`,
+// k >= kMinGraphLog; the rest directly). step_launches: kernels per step.
+template <class Step>
+dvnr_status mp_train_steps(MpCache* c, const MpParams& p, int n, int64_t left, Step& one_step,
+                           int64_t step_launches, cudaStream_t s) {
   // a lowered first-wait limit (failure-path tests) is not baked into graphs
   if (profiling_on() || p.first_wait_cycles != kWaitCycles) {
     count_eager_steps(left);
@@ -1410,7 +1324,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     }
     DVNR_CUDA(cudaGraphLaunch(c->fixed_exec[k], s));
     count_graph_replay();
-    count_launches((int64_t)(p.sched ? 3 : 2) << k);  // [schedule,] train, Adam per step
+    count_launches(step_launches << k);
     return DVNR_OK;
   };
   while (left >= G) {
@@ -1433,6 +1347,145 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   return DVNR_OK;
 }
 
+}  // namespace
+
+bool mp_supported(const dvnr_model m) {
+  const int D = m->lv.in_dim, W = m->mlp.width, F = m->lv.F;
+  if (!(W == 16 || W == 32 || W == 64)) return false;
+  if (!(F == 1 || F == 2 || F == 4 || F == 8)) return false;
+  if (D < 1 || D > 64) return false;  // padded with zeros to a multiple of 16 for layer 0
+  MpLayout lay;
+  return make_layout(m, true, lay) && make_layout(m, false, lay);
+}
+
+void mp_release(dvnr_model m) {
+  if (m->mp) {
+    MpCache* c = static_cast<MpCache*>(m->mp);
+    c->clear();
+    delete c;
+    m->mp = nullptr;
+  }
+}
+
+dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const uint32_t* slots,
+                     const dvnr_train_cfg* cfg, const AdamHyper& h, int64_t steps, bool uniform,
+                     cudaStream_t s) {
+  dvnr_model m0 = models[0];
+  MpLayout lay;
+  if (!make_layout(m0, true, lay)) {
+    set_error("FP16 path: configuration exceeds shared or tensor memory");
+    return DVNR_E_UNSUPPORTED;
+  }
+  if (!m0->mp) m0->mp = new MpCache();
+  MpCache* c = static_cast<MpCache*>(m0->mp);
+  bool hit = c->d_models && (int)c->uids.size() == n && same_cfg(c->cfg, *cfg);
+  for (int i = 0; hit && i < n; ++i)
+    hit = c->uids[i] == models[i]->uid && c->vols[i] == vols[i] && c->slots[i] == slots[i];
+  if (!hit) {
+    if (c->d_models) DVNR_CUDA(cudaStreamSynchronize(s));
+    c->clear();
+    std::vector<MpModel> hm((size_t)n);
+    std::vector<AdamModelPtrs> ha((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      dvnr_model m = models[i];
+      hm[i] = MpModel{m->theta16, m->grad, vols[i], (int32_t)m->dims[0], (int32_t)m->dims[1],
+                      (int32_t)m->dims[2], slots[i], m->st};
+      ha[i] = AdamModelPtrs{m->theta, m->m1, m->m2, m->grad, m->theta16, m->st};
+    }
+    DVNR_CUDA(dev_malloc(reinterpret_cast<void**>(&c->d_models), sizeof(MpModel) * n));
+    DVNR_CUDA(dev_malloc(reinterpret_cast<void**>(&c->d_adam), sizeof(AdamModelPtrs) * n));
+    DVNR_CUDA(dev_malloc(reinterpret_cast<void**>(&c->d_sched), sizeof(int32_t) * (2 + 2 * (size_t)n)));
+    DVNR_CUDA(cudaMemcpy(c->d_models, hm.data(), sizeof(MpModel) * n, cudaMemcpyHostToDevice));
+    DVNR_CUDA(cudaMemcpy(c->d_adam, ha.data(), sizeof(AdamModelPtrs) * n, cudaMemcpyHostToDevice));
+    c->uids.resize((size_t)n);
+    for (int i = 0; i < n; ++i) c->uids[i] = models[i]->uid;
+    c->vols.assign(vols, vols + n);
+    c->slots.assign(slots, slots + n);
+    c->cfg = *cfg;
+  }
+  MpParams p = base_params(m0, lay, cfg);
+  p.total_tiles = (int64_t)p.tiles_per_model * n;
+  p.n_models = n;
+  // equal budgets and no stop rule: every model takes part in every step, so
+  // the schedule is the identity and its kernel is left out
+  p.sched = (uniform && cfg->stop_loss == 0.f) ? nullptr : c->d_sched;
+  if (p.total_tiles * (int64_t)train_grid(p) >= (1LL << 32)) {
+    set_error("FP16 path: %lld tiles per step is beyond the supported range", (long long)p.total_tiles);
+    return DVNR_E_UNSUPPORTED;
+  }
+  p.models = c->d_models;
+  // step layout: training launch then Adam, or interleaved per wave
+  // (DVNR_INTERLEAVE=0/1 fixes it; else the autotuner picks)
+  int interleave_env = -1;
+  if (const char* e = getenv("DVNR_INTERLEAVE")) interleave_env = atoi(e) != 0 ? 1 : 0;
+  bool interleaved = false;
+  {
+    const char* at = getenv("DVNR_AUTOTUNE");
+    const bool tune = !(at && atoi(at) == 0) && !getenv("DVNR_WAVE_MODELS") && !getenv("DVNR_WAVE_TILES") &&
+                      !profiling_on() && p.first_wait_cycles == kWaitCycles;
+    const std::string key = tune_key(m0, n, cfg) + (p.sched ? ":s" : ":u");
+    TuneChoice ch{0, 0, false};
+    bool have = false;
+    if (tune) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) {
+        ch = it->second;
+        have = true;
+      }
+    }
+    if (tune && !have) {
+      const int W0 = m0->mlp.width, F0 = m0->lv.F;
+      DVNR_WF_DISPATCH(W0, F0, set_smem_attr, true, lay.smem_bytes);
+      dvnr_status rc = autotune(p, models, n, W0, F0, c->d_adam, h, interleave_env, &ch, s);
+      if (rc != DVNR_OK) return rc;
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = ch;
+      have = true;
+    }
+    if (have) {
+      p.lay.ctas_per_sm = ch.ctas_per_sm;
+      set_wave_tiles(p, ch.wave_tiles);
+      interleaved = ch.interleaved && !p.sched;
+    } else {
+      set_waves(p, m0, n);
+      interleaved = interleave_env == 1 && !p.sched;
+    }
+  }
+  if (c->any_graph() && (c->wave_tiles != p.wave_tiles || c->ctas_per_sm != p.lay.ctas_per_sm ||
+                  c->scheduled != (p.sched != nullptr) || c->interleaved != interleaved)) {
+    DVNR_CUDA(cudaStreamSynchronize(s));
+    c->drop_graph();
+  }
+  c->wave_tiles = p.wave_tiles;
+  c->ctas_per_sm = p.lay.ctas_per_sm;
+  c->scheduled = p.sched != nullptr;
+  c->interleaved = interleaved;
+  const int W = m0->mlp.width, F = m0->lv.F;
+  DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
+  auto one_step = [&](cudaStream_t st) -> dvnr_status {
+    if (interleaved) return launch_interleaved_step(p, W, F, n, c->d_adam, m0->n_store, h, st);
+    dvnr_status rc = launch_train(p, W, F, n, st);
+    if (rc != DVNR_OK) return rc;
+    return launch_adam(c->d_adam, n, m0->n_store, h, st);
+  };
+  const int64_t step_launches = interleaved ? interleaved_launches(p, n) : (p.sched ? 3 : 2);
+  int64_t left = steps;
+  if (interleaved && left > 0) {
+    // the call's first step has no pending update: it only trains, and the
+    // interleaved steps that follow apply each update before the next
+    // training of the model; the last update comes after them
+    dvnr_status rc = launch_train(p, W, F, n, s);
+    if (rc != DVNR_OK) return rc;
+    count_eager_steps(1);
+    left -= 1;
+    rc = mp_train_steps(c, p, n, left, one_step, step_launches, s);
+    if (rc != DVNR_OK) return rc;
+    return launch_adam(c->d_adam, n, m0->n_store, h, s);
+  }
+  return mp_train_steps(c, p, n, left, one_step, step_launches, s);
+}
+
 dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* cfg, uint32_t iter,
                           float S, const MpStepDebug& dbg, cudaStream_t s) {
   MpLayout lay;
@@ -1443,8 +1496,11 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
   MpModel hm{m->theta16, m->grad, vol, (int32_t)m->dims[0], (int32_t)m->dims[1], (int32_t)m->dims[2],
              0u, m->st};
   MpModel* d = nullptr;
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), sizeof(MpModel), s));
-  DVNR_CUDA(cudaMemcpyAsync(d, &hm, sizeof(MpModel), cudaMemcpyHostToDevice, s));
+  DVNR_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d), sizeof(MpModel), s));
+  if (const cudaError_t e = cudaMemcpyAsync(d, &hm, sizeof(MpModel), cudaMemcpyHostToDevice, s); e != cudaSuccess) {
+    dev_free_async(d, s);
+    return cuda_status(e, "model descriptor");
+  }
   MpParams p = base_params(m, lay, cfg);
   p.total_tiles = p.tiles_per_model;
   p.n_models = 1;
@@ -1464,7 +1520,7 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
   const int W = m->mlp.width, F = m->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
   dvnr_status rc = launch_train(p, W, F, 1, s);
-  cudaFreeAsync(d, s);
+  dev_free_async(d, s);
   DVNR_CUDA(cudaStreamSynchronize(s));  // the host descriptor is released on return
   return rc;
 }
@@ -1479,8 +1535,50 @@ dvnr_status mp_decode(dvnr_model m, const float* xyz, int64_t n, int grid_mode, 
   return mp_decode_impl(m, xyz, n, grid_mode, nullptr, nullptr, 0, 0, out, s);
 }
 
+dvnr_status mp_forward(dvnr_model m, const uint32_t* coords, int64_t n, float* y, cudaStream_t s) {
+  return mp_decode_impl(m, nullptr, n, 3, nullptr, nullptr, 0, 0, y, s, coords);
+}
+
+dvnr_status mp_backward(dvnr_model m, const uint32_t* coords, const float* dy, int64_t n,
+                        const float* scale_dev, float* dx0, cudaStream_t s) {
+  MpLayout lay;
+  if (!make_layout(m, true, lay)) {
+    set_error("FP16 path: configuration exceeds shared or tensor memory");
+    return DVNR_E_UNSUPPORTED;
+  }
+  MpModel hm{m->theta16, m->grad, nullptr, (int32_t)m->dims[0], (int32_t)m->dims[1], (int32_t)m->dims[2],
+             0u, m->st};
+  MpModel* d = nullptr;
+  DVNR_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d), sizeof(MpModel), s));
+  if (const cudaError_t e = cudaMemcpyAsync(d, &hm, sizeof(MpModel), cudaMemcpyHostToDevice, s); e != cudaSuccess) {
+    dev_free_async(d, s);
+    return cuda_status(e, "model descriptor");
+  }
+  dvnr_train_cfg cfg{};
+  cfg.batch = (int32_t)n;
+  cfg.loss = DVNR_LOSS_L2;
+  MpParams p = base_params(m, lay, &cfg);
+  p.total_tiles = p.tiles_per_model;
+  p.n_models = 1;
+  p.sched = nullptr;
+  p.models = d;
+  p.explicit_iter = 1;
+  p.ext_coords = coords;
+  p.ext_dy = dy;
+  p.ext_scale = scale_dev;
+  p.dbg_dx0 = dx0;
+  set_waves(p, m, 1);
+  const int W = m->mlp.width, F = m->lv.F;
+  DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
+  dvnr_status rc = launch_train(p, W, F, 1, s);
+  dev_free_async(d, s);
+  DVNR_CUDA(cudaStreamSynchronize(s));  // the host descriptor is released on return
+  return rc;
+}
+
 dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_mode, const RayFrame* rf,
-                           const RayBlock* rb, int64_t r0, int64_t nr, float* out, cudaStream_t s) {
+                           const RayBlock* rb, int64_t r0, int64_t nr, float* out, cudaStream_t s,
+                           const uint32_t* coords) {
   if (n <= 0) return DVNR_OK;
   MpLayout lay;
   if (!make_layout(m, false, lay)) {
@@ -1498,6 +1596,7 @@ dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_m
   p.n = n;
   p.n_tiles = (n + kTile - 1) / kTile;
   p.xyz = xyz;
+  p.coords = coords;
   p.grid_mode = grid_mode;
   for (int a = 0; a < 3; ++a) {
     p.e[a] = m->box.hi[a] - m->box.lo[a];
@@ -1548,7 +1647,7 @@ extern "C" dvnr_status dvnr_selftest_umma(int32_t* mismatches_host) {
     return DVNR_E_INVALID;
   }
   int32_t* d = nullptr;
-  DVNR_CUDA(cudaMalloc(&d, 5 * sizeof(int32_t)));
+  DVNR_CUDA(dev_malloc(reinterpret_cast<void**>(&d), 5 * sizeof(int32_t)));
   cudaError_t e = cudaMemset(d, 0, 5 * sizeof(int32_t));
   if (e == cudaSuccess) {
     ProfScope ps("umma_selftest", 0);
@@ -1557,7 +1656,7 @@ extern "C" dvnr_status dvnr_selftest_umma(int32_t* mismatches_host) {
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(mismatches_host, d, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost);
-  cudaFree(d);
+  dev_free(d);
   if (e != cudaSuccess) return cuda_status(e, "dvnr_selftest_umma");
   return mismatches_host[4] ? DVNR_E_TIMEOUT : DVNR_OK;
 }

@@ -37,6 +37,16 @@ dvnr_status mp_decode(dvnr_model m, const float* xyz, int64_t n, int grid_mode, 
 dvnr_status mp_decode_rays(dvnr_model m, const RayFrame& rf, const RayBlock& rb, int64_t r0, int64_t nr,
                            float* out, cudaStream_t s);
 dvnr_status mp_decode_impl(dvnr_model m, const float* xyz, int64_t n, int grid_mode, const RayFrame* rf,
-                           const RayBlock* rb, int64_t r0, int64_t nr, float* out, cudaStream_t s);
+                           const RayBlock* rb, int64_t r0, int64_t nr, float* out, cudaStream_t s,
+                           const uint32_t* coords = nullptr);
+// Network output y (normalised units, no value range applied) at n given
+// fixed-point coordinates (n x 3), FP16 tables and weights.
+dvnr_status mp_forward(dvnr_model m, const uint32_t* coords, int64_t n, float* y, cudaStream_t s);
+// Backward of the training kernel at n given fixed-point coordinates with the
+// upstream gradient dy (n values) instead of a loss, loss scale *scale_dev:
+// gradients left (scaled) in m->grad, dL/d(encoding) (unscaled, n x D) in
+// dx0 when not null. Synchronises the stream.
+dvnr_status mp_backward(dvnr_model m, const uint32_t* coords, const float* dy, int64_t n,
+                        const float* scale_dev, float* dx0, cudaStream_t s);
 
 }  // namespace dvnr

@@ -179,16 +179,17 @@ dvnr_status render_inr(const dvnr_model* models, int n, const float* frame_lo, c
   float4* part = nullptr;
   float* values = nullptr;
   uint32_t* coords = nullptr;
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dblocks), blocks.size() * sizeof(InrBlock), s));
-  DVNR_CUDA(cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(InrBlock),
-                            cudaMemcpyHostToDevice, s));
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&part), (size_t)std::max<int64_t>(n_ray, 1) * sizeof(float4), s));
-  dvnr_status rc = DVNR_OK;
-  if (max_chunk > 0) {
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&values), (size_t)max_chunk * 4, s);
-    if (e == cudaSuccess && !fp16) e = cudaMallocAsync(reinterpret_cast<void**>(&coords), (size_t)max_chunk * 12, s);
-    if (e != cudaSuccess) rc = cuda_status(e, "render_inr workspace");
+  // work memory; on a failure every buffer allocated so far is released below
+  cudaError_t e0 = dev_malloc_async(reinterpret_cast<void**>(&dblocks), blocks.size() * sizeof(InrBlock), s);
+  if (e0 == cudaSuccess)
+    e0 = cudaMemcpyAsync(dblocks, blocks.data(), blocks.size() * sizeof(InrBlock), cudaMemcpyHostToDevice, s);
+  if (e0 == cudaSuccess)
+    e0 = dev_malloc_async(reinterpret_cast<void**>(&part), (size_t)std::max<int64_t>(n_ray, 1) * sizeof(float4), s);
+  if (e0 == cudaSuccess && max_chunk > 0) {
+    e0 = dev_malloc_async(reinterpret_cast<void**>(&values), (size_t)max_chunk * 4, s);
+    if (e0 == cudaSuccess && !fp16) e0 = dev_malloc_async(reinterpret_cast<void**>(&coords), (size_t)max_chunk * 12, s);
   }
+  dvnr_status rc = e0 == cudaSuccess ? DVNR_OK : cuda_status(e0, "render_inr workspace");
   for (int j = 0; j < n && rc == DVNR_OK; ++j) {
     const InrBlock& bk = blocks[(size_t)j];
     const RayBlock& rb = bk.rb;
@@ -224,10 +225,10 @@ dvnr_status render_inr(const dvnr_model* models, int n, const float* frame_lo, c
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_status(e, "render_inr");
   }
-  if (coords) cudaFreeAsync(coords, s);
-  if (values) cudaFreeAsync(values, s);
-  cudaFreeAsync(part, s);
-  cudaFreeAsync(dblocks, s);
+  dev_free_async(coords, s);
+  dev_free_async(values, s);
+  dev_free_async(part, s);
+  dev_free_async(dblocks, s);
   if (rc == DVNR_OK) DVNR_CUDA(cudaStreamSynchronize(s));  // the host block table is released
   return rc;
 }
@@ -258,16 +259,16 @@ dvnr_status composite(const float* const* rgba, const int* order, int n, int64_t
   std::vector<const float4*> ptrs((size_t)n);
   for (int i = 0; i < n; ++i) ptrs[(size_t)i] = reinterpret_cast<const float4*>(rgba[order[i]]);
   const float4** d = nullptr;
-  DVNR_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&d), (size_t)n * sizeof(float4*), s));
-  DVNR_CUDA(cudaMemcpyAsync(d, ptrs.data(), (size_t)n * sizeof(float4*), cudaMemcpyHostToDevice, s));
+  DVNR_CUDA(dev_malloc_async(reinterpret_cast<void**>(&d), (size_t)n * sizeof(float4*), s));
+  cudaError_t e = cudaMemcpyAsync(d, ptrs.data(), (size_t)n * sizeof(float4*), cudaMemcpyHostToDevice, s);
   dvnr_status rc = DVNR_OK;
-  {
+  if (e == cudaSuccess) {
     ProfScope ps("composite", s);
     k_composite<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(d, n, npix, reinterpret_cast<float4*>(out));
+    e = cudaGetLastError();
   }
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) rc = cuda_status(e, "composite");
-  cudaFreeAsync(d, s);
+  dev_free_async(d, s);
   if (rc == DVNR_OK) DVNR_CUDA(cudaStreamSynchronize(s));  // the host pointer table is released
   return rc;
 }

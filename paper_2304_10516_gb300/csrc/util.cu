@@ -163,12 +163,16 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
   ModelState* st = md.st;
   if (h.gated && !model_active(st)) return;  // budget spent or stopped: no work, no counters
   const uint32_t ov = *((volatile uint32_t*)&st->overflow);
-  const bool skip = ov != 0u;
+  const bool skip = ov != 0u && !h.dry;
   const float S = h.mixed ? st->loss_scale : 1.0f;
   const float inv_S = 1.0f / S;
   const uint32_t t = st->adam_t + 1u;
-  const float bc1 = 1.0f - powf(h.beta1, (float)t);
-  const float bc2 = 1.0f - powf(h.beta2, (float)t);
+  // bias corrections 1 - beta^t. Formed as 1 - powf(beta, t) they cancel:
+  // one rounding of beta2^t near 1 is up to ~1.5e-5 of 1 - beta2^t in the
+  // first steps (beta2 = 0.999). With beta = 1 - d (d exact for beta >= 1/2)
+  // 1 - beta^t = -expm1(t log1p(-d)), which keeps a few ulps.
+  const float bc1 = -expm1f((float)t * log1pf(-(1.0f - h.beta1)));
+  const float bc2 = -expm1f((float)t * log1pf(-(1.0f - h.beta2)));
   const float ib1 = 1.0f - h.beta1, ib2 = 1.0f - h.beta2;
   const int64_t n4 = n >> 2;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -187,12 +191,14 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
       float* tp = &th.x;
       float* ap = &a.x;
       float* bp = &b.x;
+      if (!h.dry) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float gg = gp[j] * inv_S + h.weight_decay * tp[j];
-        ap[j] = h.beta1 * ap[j] + ib1 * gg;
-        bp[j] = h.beta2 * bp[j] + ib2 * gg * gg;
-        tp[j] -= h.lr * (ap[j] / bc1) / (sqrtf(bp[j] / bc2) + h.eps);
+        for (int j = 0; j < 4; ++j) {
+          const float gg = gp[j] * inv_S + h.weight_decay * tp[j];
+          ap[j] = h.beta1 * ap[j] + ib1 * gg;
+          bp[j] = h.beta2 * bp[j] + ib2 * gg * gg;
+          tp[j] -= h.lr * (ap[j] / bc1) / (sqrtf(bp[j] / bc2) + h.eps);
+        }
       }
       __stcs(th4 + i, th);
       __stcs(m14 + i, a);
@@ -204,9 +210,9 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
     }
     for (int64_t i = 4 * n4 + tid; i < n; i += stride) {
       const float gg = md.grad[i] * inv_S + h.weight_decay * md.theta[i];
-      const float a = h.beta1 * md.m1[i] + ib1 * gg;
-      const float b = h.beta2 * md.m2[i] + ib2 * gg * gg;
-      const float th = md.theta[i] - h.lr * (a / bc1) / (sqrtf(b / bc2) + h.eps);
+      const float a = h.dry ? md.m1[i] : h.beta1 * md.m1[i] + ib1 * gg;
+      const float b = h.dry ? md.m2[i] : h.beta2 * md.m2[i] + ib2 * gg * gg;
+      const float th = h.dry ? md.theta[i] : md.theta[i] - h.lr * (a / bc1) / (sqrtf(b / bc2) + h.eps);
       md.m1[i] = a;
       md.m2[i] = b;
       md.theta[i] = th;
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(kThreads) k_adam(const AdamModelPtrs* __restri
     for (int64_t i = 4 * n4 + tid; i < n; i += stride) md.grad[i] = 0.f;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !h.dry) {
     __threadfence();
     const uint32_t done = atomicAdd(&st->done_blocks, 1u);
     if (done == gridDim.x - 1) {
@@ -290,7 +296,9 @@ __global__ void k_begin_call(ModelState* st, uint32_t budget) {
 // grad_out = grad / S, loss_out = loss_sum / B; then clear the accumulators.
 __global__ void k_finish_grad(float* __restrict__ grad, int64_t n_params,
                               LayoutMap lmap, float inv_S, float* __restrict__ grad_out,
-                              ModelState* st, float inv_batch, float* __restrict__ loss_out) {
+                              ModelState* st, float inv_batch, float* __restrict__ loss_out,
+                              const float* __restrict__ scale_dev) {
+  if (scale_dev) inv_S = 1.0f / *scale_dev;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   // each storage entry belongs to one compact index, read and cleared by the
@@ -329,6 +337,48 @@ __global__ void k_load_grad(float* __restrict__ grad, const float* __restrict__ 
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->overflow, kNonFiniteGrad);
 }
 
+// Loss scale of a backward at given points: one block, max |dy| over n.
+__global__ void __launch_bounds__(kThreads) k_ext_scale(const float* __restrict__ dy, int64_t n,
+                                                        ModelState* st) {
+  float mx = 0.f;
+  bool bad = false;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const float v = fabsf(dy[i]);
+    bad |= !isfinite(v);
+    mx = fmaxf(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float sm[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < kThreads / 32; ++w) mx = fmaxf(mx, sm[w]);
+    float S = 1.0f;
+    if (!bad && mx > 0.f) {
+      int e = 0;
+      frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1): 2^(1-e) puts the largest scaled value in [1, 2)
+      e = 1 - e;
+      e = e < -24 ? -24 : (e > 40 ? 40 : e);
+      S = ldexpf(1.0f, e);
+    }
+    st->ext_scale = S;
+  }
+}
+
+__global__ void k_set_ext_scale(ModelState* st, float S) { st->ext_scale = S; }
+
+// theta[storage j] = params[compact i] and its binary16 copy.
+__global__ void k_load_params(float* __restrict__ theta, __half* __restrict__ theta16,
+                              const float* __restrict__ params, int64_t n_params, LayoutMap lmap) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_params;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = ext_to_int(lmap, i);
+    const float v = params[i];
+    theta[j] = v;
+    theta16[j] = __float2half_rn(v);
+  }
+}
+
 __global__ void k_state_set_scale(ModelState* st, float loss_scale) {
   st->loss_scale = loss_scale;
   st->good_steps = 0u;
@@ -360,7 +410,7 @@ dvnr_status launch_finish_grad(dvnr_model m, float loss_scale_used, float inv_ba
     ProfScope ps_("finish_grad", s);
     k_finish_grad<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(
       m->grad, m->n_params, m->lmap, 1.0f / loss_scale_used, grad_out, m->st,
-      inv_batch, loss_out);
+      inv_batch, loss_out, nullptr);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;
@@ -371,6 +421,38 @@ dvnr_status launch_load_grad(dvnr_model m, const float* grad_in, bool mixed, cud
     ProfScope ps_("load_grad", s);
     k_load_grad<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(m->grad, grad_in, m->n_params, m->lmap,
                                                                      m->st, mixed ? 1 : 0);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_ext_scale(dvnr_model m, const float* dy, int64_t n, float loss_scale, cudaStream_t s) {
+  {
+    ProfScope ps_("ext_scale", s);
+    if (loss_scale > 0.f)
+      k_set_ext_scale<<<1, 1, 0, s>>>(m->st, loss_scale);
+    else
+      k_ext_scale<<<1, kThreads, 0, s>>>(dy, n, m->st);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_load_params(dvnr_model m, const float* params, cudaStream_t s) {
+  {
+    ProfScope ps_("load_params", s);
+    k_load_params<<<grid_for(m->n_params, kThreads), kThreads, 0, s>>>(m->theta, m->theta16, params,
+                                                                       m->n_params, m->lmap);
+  }
+  DVNR_CUDA(cudaGetLastError());
+  return DVNR_OK;
+}
+
+dvnr_status launch_finish_grad_dev(dvnr_model m, const float* scale_dev, float* grad_out, cudaStream_t s) {
+  {
+    ProfScope ps_("finish_grad", s);
+    k_finish_grad<<<grid_for(m->n_store, kThreads), kThreads, 0, s>>>(
+      m->grad, m->n_params, m->lmap, 1.0f, grad_out, m->st, 0.f, nullptr, scale_dev);
   }
   DVNR_CUDA(cudaGetLastError());
   return DVNR_OK;

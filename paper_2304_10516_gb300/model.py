@@ -255,6 +255,37 @@ class Model:
         c = cfg.to_c()
         A.call("dvnr_adam_step", self._h, _ptr(g), C.byref(c), _stream(stream))
 
+    def params_tensor(self, device="cuda"):
+        """The FP32 master weights as a float32 CUDA tensor (compact layout),
+        e.g. as the params argument of EncodeMLP."""
+        import torch
+
+        return torch.from_numpy(self.get_weights()).to(device)
+
+    def forward(self, coords, precision=A.DVNR_FP32, stream=None):
+        """Network output (normalised units) at fixed-point coordinates (n, 3)."""
+        import torch
+
+        coords = coords.contiguous()
+        y = torch.empty(coords.shape[0], dtype=torch.float32, device=coords.device)
+        A.call("dvnr_forward", self._h, _ptr(coords), coords.shape[0], int(precision), _ptr(y),
+               _stream(stream))
+        return y
+
+    def backward(self, coords, dy, precision=A.DVNR_FP32, loss_scale=0.0, want_dx0=False, stream=None):
+        """(gradient of all parameters (compact), dL/d(encoding) or None) for
+        the upstream gradient dy at fixed-point coordinates (n, 3)."""
+        import torch
+
+        coords = coords.contiguous()
+        d = dy.detach().to(torch.float32).contiguous()
+        g = torch.empty(self.n_params, dtype=torch.float32, device=coords.device)
+        dx0 = (torch.empty((coords.shape[0], self.enc.n_levels * self.enc.n_features),
+                           dtype=torch.float32, device=coords.device) if want_dx0 else None)
+        A.call("dvnr_backward", self._h, _ptr(coords), coords.shape[0], _ptr(d), int(precision),
+               float(loss_scale), _ptr(g), _ptr(dx0), _stream(stream))
+        return g, dx0
+
     def moments(self):
         """(m1, m2): the Adam moments in the compact layout (host arrays)."""
         m1 = np.empty(self.n_params, dtype=np.float32)
@@ -288,6 +319,69 @@ class Model:
         out = torch.empty((n, self.enc.n_levels, 8), dtype=torch.int32, device=coords.device)
         A.call("dvnr_corner_indices", self._h, _ptr(coords), n, _ptr(out), _stream(stream))
         return out
+
+
+def _encode_mlp_class():
+    import torch
+
+    class EncodeMLP(torch.autograd.Function):
+        """y = f(params; coords): the hash-grid encoding and ReLU MLP of a
+        model (Sec. 3) as a differentiable function of its parameters, run by
+        the library's kernels (dvnr_forward / dvnr_backward).
+
+        apply(params, coords, model, precision=DVNR_FP32, loss_scale=0.0)
+          params  float32 CUDA tensor of model.n_params values, the compact
+                  layout (tables level by level, then W_0 .. W_{H-1}, w_out);
+                  loaded into the model before the forward and again before
+                  the backward, so it is the source of truth
+          coords  int32/uint32 CUDA tensor (n, 3) of fixed-point coordinates
+                  m in [0, 2^24] (u = m 2^-24), not differentiable
+          returns y, a float32 tensor (n,) in normalised units.
+        The gradient with respect to params comes from the fused training
+        kernel with the loss replaced by the incoming dL/dy."""
+
+        @staticmethod
+        def forward(ctx, params, coords, model, precision=A.DVNR_FP32, loss_scale=0.0):
+            assert params.is_cuda and params.dtype == torch.float32 and params.numel() == model.n_params
+            coords = coords.contiguous()
+            assert coords.is_cuda and coords.dim() == 2 and coords.shape[1] == 3
+            p = params.detach().contiguous()
+            stream = _stream(None)
+            A.call("dvnr_load_params", model.handle, _ptr(p), stream)
+            y = torch.empty(coords.shape[0], dtype=torch.float32, device=coords.device)
+            A.call("dvnr_forward", model.handle, _ptr(coords), coords.shape[0], int(precision), _ptr(y),
+                   stream)
+            ctx.save_for_backward(p, coords)
+            ctx.model, ctx.precision, ctx.loss_scale = model, int(precision), float(loss_scale)
+            return y
+
+        @staticmethod
+        def backward(ctx, dy):
+            p, coords = ctx.saved_tensors
+            m = ctx.model
+            stream = _stream(None)
+            A.call("dvnr_load_params", m.handle, _ptr(p), stream)
+            g = torch.empty(m.n_params, dtype=torch.float32, device=p.device)
+            d = dy.detach().to(torch.float32).contiguous()
+            A.call("dvnr_backward", m.handle, _ptr(coords), coords.shape[0], _ptr(d), ctx.precision,
+                   ctx.loss_scale, _ptr(g), None, stream)
+            return g, None, None, None, None
+
+    return EncodeMLP
+
+
+_ENCODE_MLP = None
+
+
+def __getattr__(name):
+    # EncodeMLP subclasses a torch class: built on first use, so that importing
+    # this module does not import torch
+    global _ENCODE_MLP
+    if name == "EncodeMLP":
+        if _ENCODE_MLP is None:
+            _ENCODE_MLP = _encode_mlp_class()
+        return _ENCODE_MLP
+    raise AttributeError(name)
 
 
 def train(models, volumes, cfg: TrainConfig, stream=None, sync: bool = True):

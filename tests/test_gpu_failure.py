@@ -98,7 +98,10 @@ def test_training_recovers_after_a_timeout(dv, A):
     c, (a, ref) = _models(dv, 2, seed=50)
     ref.set_weights(a.get_weights())
     vol = _vol()
-    cfg = dv.TrainConfig(batch=c["batch"], steps=1, precision=A.DVNR_FP16, seed=3)
+    # lr 5e-4: a stable regime, where a shift of the sample stream by one
+    # iteration moves the 200-step PSNR little (at 1e-2 training is chaotic)
+    cfg = dv.TrainConfig(batch=c["batch"], steps=1, lr=5e-4, precision=A.DVNR_FP16, seed=3)
+    p0 = _psnr(dv, a, vol)
     A.call("dvnr_debug_first_wait", 0, None)
     try:
         with pytest.raises(A.DvnrError):
@@ -115,8 +118,8 @@ def test_training_recovers_after_a_timeout(dv, A):
     assert rc == 0
     assert s["adam_t"] == 200 and s["skipped"] == 1 and s["iter"] == 201
     pa, pr = _psnr(dv, a, vol), _psnr(dv, ref, vol)
-    assert abs(pa - pr) < 0.5, (pa, pr)
-    assert pa > 25.0
+    assert abs(pa - pr) < 0.2, (pa, pr)
+    assert pa > p0 + 10.0
     a.close()
     ref.close()
 
@@ -159,3 +162,86 @@ def test_grouped_call_after_a_model_is_replaced(dv, A):
     assert not np.array_equal(n.get_weights(), w_n)
     a.close()
     n.close()
+
+
+def _live(A):
+    c, b = C.c_int64(), C.c_int64()
+    A.call("dvnr_debug_live_allocs", C.byref(c), C.byref(b))
+    return c.value, b.value
+
+
+def _scenario_models(dv, A):
+    """Model lifecycle through every call that allocates device memory:
+    creation, a grouped FP16 call (descriptor cache and step graphs), decode,
+    grid and network rendering, compositing, the FP64 error reduction, a
+    backward at given points, freezing, and the FP32 path's workspaces."""
+    enc = dv.EncodingConfig(4, 2, 10, 4, 1.5)
+    mlp = dv.MLPConfig(16, 2)
+    vol = _vol()[:18, :18, :18].contiguous()
+    models = []
+    try:
+        for lo in ((0, 0, 0), (0, 0, 16)):
+            models.append(dv.Model(lo, (16, 16, lo[2] + 16), 1, enc, mlp, seed=3))
+        a, b = models
+        dv.train([a, b], [vol, vol], dv.TrainConfig(batch=1000, steps=9, precision=A.DVNR_FP16, seed=1))
+        g = a.decode_grid()
+        tf = dv.make_tf()
+        img = dv.render([a, b], tf, 24, 24, 16)
+        img2 = dv.render_inr([a, b], tf, 24, 24, 16)
+        dv.composite([img, img2], [0.0, 1.0])
+        dv.error_stats(g, vol[1:-1, 1:-1, 1:-1].contiguous())
+        coords = torch.randint(0, 1 << 24, (300, 3), dtype=torch.int32, device="cuda")
+        b.backward(coords, torch.ones(300, device="cuda") / 300, A.DVNR_FP16)
+        a.freeze()
+        a.decode_grid()
+        dv.train([b], [vol], dv.TrainConfig(batch=500, steps=2, precision=A.DVNR_FP32, seed=1))
+        b.decode_points(torch.rand(100, 3, device="cuda") * 16)
+        dv.render_inr([b], tf, 24, 24, 16)
+        b.backward(coords, torch.ones(300, device="cuda") / 300, A.DVNR_FP32)
+    finally:
+        for m in models:
+            m.close()
+
+
+def _scenario_window(dv, A):
+    """A temporal window of two partitions pushed three times into a window
+    of two steps: model creation, warm starts, training, freezing, eviction."""
+    enc = dv.EncodingConfig(4, 2, 10, 4, 1.5)
+    vol = _vol()[:18, :18, :18].contiguous()
+    w = dv.Window([((0, 0, 0), (16, 16, 16)), ((0, 0, 16), (16, 16, 32))], 2, enc, dv.MLPConfig(16, 2),
+                  ghost=1, seed=5)
+    try:
+        for _ in range(3):
+            w.push([vol, vol], dv.TrainConfig(batch=600, steps=3, precision=A.DVNR_FP16, seed=2))
+    finally:
+        w.close()
+
+
+@pytest.mark.parametrize("scenario", [_scenario_models, _scenario_window])
+def test_failed_allocations_release_everything(dv, A, scenario):
+    # the nth device allocation fails, for n = 1, 2, ... until the scenario
+    # runs through: every failure is reported as DVNR_E_OOM and, once the
+    # scenario's objects are closed, the library holds no more device memory
+    # than before
+    scenario(dv, A)  # once without failures (compiles, autotunes)
+    torch.cuda.synchronize()
+    base = _live(A)
+    failures = 0
+    for n in range(1, 400):
+        A.call("dvnr_debug_fail_alloc", n)
+        try:
+            scenario(dv, A)
+            done = True
+        except A.DvnrError as e:
+            assert e.status == 2, (n, str(e))  # DVNR_E_OOM
+            done = False
+            failures += 1
+        finally:
+            A.call("dvnr_debug_fail_alloc", 0)
+        torch.cuda.synchronize()
+        assert _live(A) == base, (scenario.__name__, n, _live(A), base)
+        if done:
+            break
+    else:
+        pytest.fail("the scenario never ran through")
+    assert failures >= 5  # the scenario allocates, and each allocation was made to fail once
