@@ -186,14 +186,20 @@ def test_fp16_training_equal_psnr(dv, orc, A):
 
 @pytest.mark.parametrize("wave_models", [None, "1", "3", "tiles:7"])
 def test_grouped_launch_models_are_independent(dv, A, monkeypatch, wave_models):
-    # Four models in one grouped FP16 launch. Model 0 trained in the group
-    # equals model 0 trained alone (same RNG slot) up to the reordering of
-    # atomic sums, and perturbing model 2's volume leaves the other models
-    # within that same reordering noise.
+    # Four models in one grouped FP16 launch. Compared after one step through
+    # the first Adam moment, m1 = (1 - beta1) g: linear in the step's
+    # gradient (the weights are not -- Adam's first steps move every entry by
+    # about lr sign(g), so an entry whose gradient is at the level of the
+    # atomic reordering noise moves by up to 2 lr between runs), and the
+    # step's forward is bit-identical between runs (same initial weights).
+    # Model 0 trained in the group equals model 0 trained alone (same RNG
+    # slot) up to the reordering of atomic sums, and perturbing model 2's
+    # volume leaves the other models within that same noise. Then 10 steps:
+    # the unperturbed models' PSNRs do not move.
     from paper_2304_10516_gb300 import volumes
 
     # wave_models: models trained per wave inside the launch (1: one model at
-    # a time; 3: waves of 3 + 1); None leaves the library's choice (one wave)
+    # a time; 3: waves of 3 + 1); None leaves the library's choice
     # ("tiles:7": waves of 7 tiles, which split the models' tile runs mid-model)
     if wave_models and wave_models.startswith("tiles:"):
         monkeypatch.setenv("DVNR_WAVE_TILES", wave_models[6:])
@@ -202,25 +208,41 @@ def test_grouped_launch_models_are_independent(dv, A, monkeypatch, wave_models):
     c = dict(P.configs_blobs64(), batch=2048)
     vols = [torch.from_numpy(volumes.blobs(32, seed=2000 + i)).cuda() for i in range(4)]
 
-    def group(vs, steps=10):
+    def group(vs, steps):
         ms = [_model(dv, c, seed=50 + i, hi=(32, 32, 32)) for i in range(4)]
         dv.train(ms, vs, dv.TrainConfig(batch=2048, steps=steps, lr=1e-3, seed=5,
                                         precision=A.DVNR_FP16))
-        return [m.get_weights() for m in ms]
+        return ms
 
-    base = group(vols)
-    again = group(vols)
+    def m1_of(ms):
+        return [m.moments()[0] for m in ms]
+
+    base = m1_of(group(vols, 1))
+    again = m1_of(group(vols, 1))
     noise = max(np.linalg.norm(a - b) for a, b in zip(base, again))
     pert = list(vols)
     pert[2] = vols[2] ** 2  # a non-affine change (min/max normalisation hides affine ones)
-    moved = group(pert)
+    moved = m1_of(group(pert, 1))
+    ref = max(np.linalg.norm(b) for b in base)
     for j in (0, 1, 3):
-        assert np.linalg.norm(moved[j] - base[j]) <= 3 * noise + 1e-6, j
-    assert np.linalg.norm(moved[2] - base[2]) > 10 * noise + 1e-4
+        assert np.linalg.norm(moved[j] - base[j]) <= 3 * noise + 1e-6 * ref, j
+    assert np.linalg.norm(moved[2] - base[2]) > 10 * noise + 1e-4 * ref
     alone = _model(dv, c, seed=50, hi=(32, 32, 32))
-    dv.train([alone], [vols[0]], dv.TrainConfig(batch=2048, steps=10, lr=1e-3, seed=5,
+    dv.train([alone], [vols[0]], dv.TrainConfig(batch=2048, steps=1, lr=1e-3, seed=5,
                                                 precision=A.DVNR_FP16))
-    assert np.linalg.norm(alone.get_weights() - base[0]) <= 3 * noise + 1e-6
+    assert np.linalg.norm(alone.moments()[0] - base[0]) <= 3 * noise + 1e-6 * ref
+
+    def psnrs(ms, vs):
+        out = []
+        for m, v in zip(ms, vs):
+            sse, _ = dv.error_stats(m.decode_grid(), v)
+            out.append(P.psnr(sse / v.numel()))
+        return out
+
+    p_base = psnrs(group(vols, 10), vols)
+    p_moved = psnrs(group(pert, 10), pert)
+    for j in (0, 1, 3):
+        assert abs(p_moved[j] - p_base[j]) < 0.05, (j, p_moved[j], p_base[j])
 
 
 def test_fp16_overflow_skips_step_and_halves_scale(dv, A):
@@ -236,3 +258,49 @@ def test_fp16_overflow_skips_step_and_halves_scale(dv, A):
     assert st["skipped"] == 3 and st["adam_t"] == 0
     assert st["loss_scale"] == 1024.0 / 8
     np.testing.assert_array_equal(m.get_weights(), w.astype(np.float32))
+
+
+@pytest.mark.parametrize("name", ["blobs64", "w64d32h3"])
+def test_fp16_error_against_plain_fp64_oracle(dv, orc, A, name):
+    # The production path against the FP64 oracle without FP16 emulation: the
+    # error the FP16 storage and tensor-core operands cost (Sec. 3.4 16-bit
+    # weights, Sec. 3.6 tensor-core training). Measured on one GB300, one step
+    # of 4096 samples (L1) with tables of the scale training reaches:
+    #   forward y         max |err| / max |y|        6.4e-4, 8.4e-4
+    #   dL/d(encoding)    normwise (kink-free rows)  4.3e-4, 6.2e-4
+    #   MLP gradients     normwise                   5.5e-4, 8.1e-4
+    #   table gradients   normwise                   6.2e-3, 2.8e-2 (rows whose
+    #                     pre-activations lie within the FP16 rounding of 0
+    #                     switch ReLU branch; the emulation comparison of
+    #                     test_fp16_step_matches_oracle bounds that part)
+    #   decode (grid)     max |err| / value range    4.9e-4, 6.7e-4
+    # The bounds are about three times those values.
+    from paper_2304_10516_gb300 import volumes
+
+    c = dict(CONFIGS.get(name, P.configs_blobs64()), batch=4096)
+    oc = P.oracle_cfg(c)
+    vol = volumes.blobs(40, seed=1001)
+    theta = orc.init_params(oc, 31).astype(np.float32)
+    theta[: oc.n_enc] = np.random.default_rng(3).uniform(-0.1, 0.1, oc.n_enc).astype(np.float32)
+    m = _model(dv, c, seed=0, hi=(40, 40, 40))
+    m.set_weights(theta)
+    out = m.train_grad(torch.from_numpy(vol).cuda(),
+                       dv.TrainConfig(batch=4096, loss=0, seed=78, precision=A.DVNR_FP16), iteration=5)
+    torch.cuda.synchronize()
+    coords = out["coords"].cpu().numpy().view(np.uint32)
+    t = orc.targets(vol, coords, float(vol.min()), float(vol.max()))
+    th64 = theta.astype(np.float64)
+    r = orc.fwd_bwd(oc, th64, coords, t, loss=0, mixed=False, want_zabs=True)
+    y = out["y"].cpu().numpy()
+    assert np.abs(y - r["y"]).max() <= 3e-3 * np.abs(r["y"]).max()
+    keep = r["zabs"].min(axis=1) > 2e-4
+    assert keep.sum() > 0.2 * len(keep)
+    P.assert_normwise(out["dx0"].cpu().numpy()[keep], r["dx0"][keep], 2e-3, what="dL/dx0 vs FP64")
+    g = out["grad"].cpu().numpy()
+    P.assert_normwise(g[oc.n_enc:], r["grad_mlp"], 3e-3, what="MLP grad vs FP64")
+    P.assert_normwise(g[: oc.n_enc], r["grad_enc"], 0.1, what="table grad vs FP64")
+    m.set_precision(A.DVNR_FP16)
+    dec = m.decode_grid().cpu().numpy()
+    ref = orc.decode_grid(oc, th64, (40, 40, 40), 0, 0.0, 1.0)
+    assert np.abs(dec - ref).max() <= 2e-3 * (ref.max() - ref.min())
+    m.close()
