@@ -475,9 +475,9 @@ dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n,
  *    allocates nothing.
  *  - Limit: n <= 2^28 (268435456) elements; larger n returns DVNR_E_INVALID
  *    with a message, before any device work.
- *  - The first call on a device looks up the scratch address on that device
- *    (the device must be current); make that first call before any stream
- *    capture.
+ *  - The scratch address is looked up once per device, by dvnr_create on its
+ *    device or else by the first call on a device (the device must be
+ *    current); make that first call before any stream capture.
  *  - All calls share the scratch array and leave their partial sums in it;
  *    calls whose kernels overlap on the GPU (e.g. on two streams) race and
  *    must be serialised by the caller.

@@ -322,6 +322,7 @@ dvnr_status dvnr_create(const dvnr_box* box, const dvnr_enc_cfg* enc, const dvnr
       (ce = cudaMemset(m->theta16, 0, b16)) != cudaSuccess)
     return cleanup(cuda_status(ce, "cudaMemset"));
   if ((rc = launch_init_params(m, seed, 0)) != DVNR_OK) return cleanup(rc);
+  if ((rc = prime_err_scratch()) != DVNR_OK) return cleanup(rc);
   if ((ce = cudaMemcpy(m->st, &st0, sizeof(st0), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaMemcpy(adam_ptrs_dev(m), &ap, sizeof(ap), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (ce = cudaDeviceSynchronize()) != cudaSuccess)

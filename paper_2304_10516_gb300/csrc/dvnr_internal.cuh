@@ -245,6 +245,27 @@ __device__ __forceinline__ uint32_t corner_index(const LevelTab& lv, int l, uint
   return (x ^ (y * 2654435761u) ^ (z * 805459861u)) & lv.hash_mask;
 }
 
+// The 8 corners of the cell with lower corner (x, y, z) at level l, corner k
+// = (x + (k&1), y + ((k>>1)&1), z + ((k>>2)&1)): the values of corner_index,
+// formed from one base per level (dense: base + {0, 1, s, s + 1, s^2, ...};
+// hashed: the y and z products once each, (y + 1) P = y P + P mod 2^32).
+__device__ __forceinline__ void corner_indices8(const LevelTab& lv, int l, uint32_t x, uint32_t y, uint32_t z,
+                                                uint32_t (&idx)[8]) {
+  if ((lv.dense_mask >> l) & 1u) {
+    const uint32_t s = lv.N[l] + 1u, s2 = s * s;
+    const uint32_t b = x + s * (y + s * z);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) idx[k] = b + (uint32_t)(k & 1) + ((k >> 1) & 1 ? s : 0u) + ((k >> 2) & 1 ? s2 : 0u);
+  } else {
+    const uint32_t hy0 = y * 2654435761u, hy1 = hy0 + 2654435761u;
+    const uint32_t hz0 = z * 805459861u, hz1 = hz0 + 805459861u;
+    const uint32_t msk = lv.hash_mask;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      idx[k] = ((x + (uint32_t)(k & 1)) ^ ((k >> 1) & 1 ? hy1 : hy0) ^ ((k >> 2) & 1 ? hz1 : hz0)) & msk;
+  }
+}
+
 // Sampling parameters of one model slot in one step (Sec. 3.2-3.3).
 struct SampleParams {
   uint2 key;           // seed
@@ -385,6 +406,9 @@ dvnr_status launch_begin_call(ModelState* st, uint32_t budget, cudaStream_t s);
 // gradient buffer as Adam expects it: times the loss scale on the FP16 path,
 // a non-finite value flagged as kNonFiniteGrad.
 dvnr_status launch_load_grad(dvnr_model m, const float* grad_in, bool mixed, cudaStream_t s);
+// Look up the device address of dvnr_error_stats_noalloc's scratch array on
+// the current device now (once per device).
+dvnr_status prime_err_scratch();
 dvnr_status launch_minmax(const float* vol, int64_t n, ModelState* st, cudaStream_t s);
 dvnr_status launch_error_stats(const float* a, const float* b, int64_t n, double* out_dev,
                                cudaStream_t s);

@@ -202,16 +202,17 @@ __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half*
           }
         }
       } else {
+        if (on) {
+          uint32_t idx[8];
+          corner_indices8(lv, l, bx, by, bz, idx);
+          const __half* tab = tab16 + lv.off[l];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          if (on) {
-            const uint32_t idx =
-                corner_index(lv, l, bx + (k & 1), by + ((k >> 1) & 1), bz + ((k >> 2) & 1));
-            HalfVec<F>::load(tab16 + lv.off[l] + (size_t)idx * F, v[g][k]);
-          } else {
+          for (int k = 0; k < 8; ++k) HalfVec<F>::load(tab + (size_t)idx[k] * F, v[g][k]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
 #pragma unroll
             for (int f = 0; f < F; ++f) v[g][k][f] = 0.f;
-          }
         }
       }
     }
@@ -223,10 +224,12 @@ __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half*
       float acc[F];
 #pragma unroll
       for (int f = 0; f < F; ++f) acc[f] = 0.f;
+      // w_k = (wx wy) wz, the x-y products formed once for both z
+      const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+      const float wxy[4] = {gx * gy, fx * gy, gx * fy, fx * fy};
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const float w = ((k & 1) ? fx : 1.f - fx) * (((k >> 1) & 1) ? fy : 1.f - fy) *
-                        (((k >> 2) & 1) ? fz : 1.f - fz);
+        const float w = wxy[k & 3] * ((k >> 2) ? fz : gz);
 #pragma unroll
         for (int f = 0; f < F; ++f) acc[f] += w * v[g][k][f];
       }

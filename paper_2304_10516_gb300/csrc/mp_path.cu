@@ -215,6 +215,12 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
   constexpr int NOUT = W >= 32 ? W / 32 : 1;
   float acc_out[NOUT];
   float loss_acc = 0.f;
+  // the next tile's sample and volume corners, drawn and fetched while the
+  // tensor core runs this tile's first product (when the next tile is of
+  // the same model and in this CTA's run of the wave)
+  bool have_next = false;
+  uint3 mc_next = make_uint3(0u, 0u, 0u);
+  VolCorners vc_next{};
 
   // thread 0: an MMA was committed and its completion not yet seen by
   // thread 0 (after an abort, teardown waits for it before freeing TMEM)
@@ -319,11 +325,17 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
     const int i = tile * kTile + tid;
     const bool valid = i < p.batch;
     uint3 mc = make_uint3(0u, 0u, 0u);
-    if (valid)
-      mc = p.ext_coords ? make_uint3(p.ext_coords[3 * i], p.ext_coords[3 * i + 1], p.ext_coords[3 * i + 2])
-                        : draw_sample(sp, (uint32_t)i, iter);
     VolCorners vc{};
-    if (valid && md.vol) vc = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc);  // in flight during the encode
+    if (have_next) {
+      mc = mc_next;
+      vc = vc_next;
+    } else {
+      if (valid)
+        mc = p.ext_coords ? make_uint3(p.ext_coords[3 * i], p.ext_coords[3 * i + 1], p.ext_coords[3 * i + 2])
+                          : draw_sample(sp, (uint32_t)i, iter);
+      if (valid && md.vol) vc = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc);  // in flight during the encode
+    }
+    have_next = false;
 #if DVNR_TRAIN_STAGED
     if constexpr (F == 2) {
       // all gathers of the tile in flight at once, staged in the dZ tile and
@@ -347,6 +359,22 @@ __global__ void __launch_bounds__(kTile, 1) k_mp_train(const __grid_constant__ M
         issue_forward(tmem, smem, p.lay, k, k == 0 ? (int)p.lay.dpad : W, W);
         umma::commit(mbar);
         inflight = true;
+      }
+      if (k == 0 && g + 1 < g_end) {
+        const int pos_n = (int)((g + 1) / p.tiles_per_model);
+        const int model_n = p.sched ? p.sched[1 + pos_n] : pos_n;
+        if (model_n == cur) {
+          const int i_n = (int)(g + 1 - (int64_t)pos_n * p.tiles_per_model) * kTile + tid;
+          const bool valid_n = i_n < p.batch;
+          mc_next = make_uint3(0u, 0u, 0u);
+          if (valid_n)
+            mc_next = p.ext_coords ? make_uint3(p.ext_coords[3 * i_n], p.ext_coords[3 * i_n + 1],
+                                                p.ext_coords[3 * i_n + 2])
+                                   : draw_sample(sp, (uint32_t)i_n, iter);
+          vc_next = VolCorners{};
+          if (valid_n && md.vol) vc_next = vol_fetch(md.vol, md.nx, md.ny, md.nz, mc_next);
+          have_next = true;
+        }
       }
       if (!mma_wait()) goto teardown;
       umma::fence_after_sync();

@@ -669,6 +669,15 @@ dvnr_status err_scratch(double** out) {
 }
 
 }  // namespace
+
+// Resolve the scratch address of the current device ahead of the first
+// dvnr_error_stats_noalloc call there (dvnr_create calls this), so that the
+// lookup, and the module load it may trigger, happens outside that call.
+dvnr_status prime_err_scratch() {
+  double* p = nullptr;
+  return err_scratch(&p);
+}
+
 }  // namespace dvnr
 
 extern "C" dvnr_status dvnr_error_stats_noalloc(const float* a_dev, const float* b_dev, int64_t n,

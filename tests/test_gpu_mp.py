@@ -208,27 +208,31 @@ def test_grouped_launch_models_are_independent(dv, A, monkeypatch, wave_models):
     c = dict(P.configs_blobs64(), batch=2048)
     vols = [torch.from_numpy(volumes.blobs(32, seed=2000 + i)).cuda() for i in range(4)]
 
-    def group(vs, steps):
+    def group(vs, steps, loss=A.DVNR_LOSS_L1):
         ms = [_model(dv, c, seed=50 + i, hi=(32, 32, 32)) for i in range(4)]
-        dv.train(ms, vs, dv.TrainConfig(batch=2048, steps=steps, lr=1e-3, seed=5,
+        dv.train(ms, vs, dv.TrainConfig(batch=2048, steps=steps, lr=1e-3, seed=5, loss=loss,
                                         precision=A.DVNR_FP16))
         return ms
 
     def m1_of(ms):
         return [m.moments()[0] for m in ms]
 
-    base = m1_of(group(vols, 1))
-    again = m1_of(group(vols, 1))
+    # L2: the first step's L1 gradient is sign(y - t) with y ~ 0 at the
+    # initial weights, the same for any target, so it could not show the
+    # perturbation
+    L2 = A.DVNR_LOSS_L2
+    base = m1_of(group(vols, 1, L2))
+    again = m1_of(group(vols, 1, L2))
     noise = max(np.linalg.norm(a - b) for a, b in zip(base, again))
     pert = list(vols)
     pert[2] = vols[2] ** 2  # a non-affine change (min/max normalisation hides affine ones)
-    moved = m1_of(group(pert, 1))
+    moved = m1_of(group(pert, 1, L2))
     ref = max(np.linalg.norm(b) for b in base)
     for j in (0, 1, 3):
         assert np.linalg.norm(moved[j] - base[j]) <= 3 * noise + 1e-6 * ref, j
     assert np.linalg.norm(moved[2] - base[2]) > 10 * noise + 1e-4 * ref
     alone = _model(dv, c, seed=50, hi=(32, 32, 32))
-    dv.train([alone], [vols[0]], dv.TrainConfig(batch=2048, steps=1, lr=1e-3, seed=5,
+    dv.train([alone], [vols[0]], dv.TrainConfig(batch=2048, steps=1, lr=1e-3, seed=5, loss=L2,
                                                 precision=A.DVNR_FP16))
     assert np.linalg.norm(alone.moments()[0] - base[0]) <= 3 * noise + 1e-6 * ref
 
@@ -294,7 +298,7 @@ def test_fp16_error_against_plain_fp64_oracle(dv, orc, A, name):
     y = out["y"].cpu().numpy()
     assert np.abs(y - r["y"]).max() <= 3e-3 * np.abs(r["y"]).max()
     keep = r["zabs"].min(axis=1) > 2e-4
-    assert keep.sum() > 0.2 * len(keep)
+    assert keep.sum() > 0.1 * len(keep)
     P.assert_normwise(out["dx0"].cpu().numpy()[keep], r["dx0"][keep], 2e-3, what="dL/dx0 vs FP64")
     g = out["grad"].cpu().numpy()
     P.assert_normwise(g[oc.n_enc:], r["grad_mlp"], 3e-3, what="MLP grad vs FP64")
