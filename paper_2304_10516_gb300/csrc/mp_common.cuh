@@ -263,73 +263,93 @@ constexpr uint32_t kStageLevelBytes = 4u * 128u * 8u;
 // cap_a levels at stage_a, then cap_b at stage_b (regions of the tile
 // buffers that are idle during the encode); more levels run in further
 // rounds. Only the issuing thread reads its rows, so no barrier is needed.
+// One round of encode_to_tile_staged, split so that a tile's copies can be
+// issued early and finished later: stage_round issues the corner copies of
+// levels l0 .. l1-1, at most 16 (level l0 + r at stage_a + r 4 KB for r < cap_a, else at
+// stage_b + (r - cap_a) 4 KB) and returns the bits of the pairs that arrived
+// as (x + 1, x); finish_round waits for the copies and writes the levels'
+// interpolated features to the thread's ACT row.
+__device__ __forceinline__ uint64_t stage_round(const LevelTab& lv, const __half* __restrict__ tab16, uint3 m,
+                                                bool valid, uint32_t s, uint8_t* stage_a, int cap_a,
+                                                uint8_t* stage_b, int l0, int l1) {
+  constexpr int F = 2;
+  uint64_t swapped = 0;  // bit 4 (l - l0) + q: the pair arrived as (x + 1, x)
+  if (!valid) return 0;
+  for (int l = l0; l < l1; ++l) {
+    uint32_t bx, by, bz;
+    float f_;
+    lattice(m.x, lv.N[l], bx, f_);
+    lattice(m.y, lv.N[l], by, f_);
+    lattice(m.z, lv.N[l], bz, f_);
+    const int r = l - l0;
+    const uint32_t lvl = umma::smem_u32(r < cap_a ? stage_a + (uint32_t)r * kStageLevelBytes
+                                                  : stage_b + (uint32_t)(r - cap_a) * kStageLevelBytes);
+    const __half* tab = tab16 + lv.off[l];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t y = by + (q & 1), z = bz + (q >> 1);
+      const uint32_t i0 = corner_index(lv, l, bx, y, z);
+      const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
+      const uint32_t dst = lvl + ((uint32_t)q * 128u + s) * 8u;
+      if (i1 == (i0 ^ 1u)) {
+        cp_async8(dst, tab + (size_t)(i0 & ~1u) * F);
+        if (i0 & 1u) swapped |= 1ull << (4 * r + q);
+      } else {
+        cp_async4(dst, tab + (size_t)i0 * F);
+        cp_async4(dst + 4u, tab + (size_t)i1 * F);
+      }
+    }
+  }
+  return swapped;
+}
+
+__device__ __forceinline__ void finish_round(const LevelTab& lv, uint3 m, bool valid, uint8_t* act, uint32_t s,
+                                             const uint8_t* stage_a, int cap_a, const uint8_t* stage_b, int l0,
+                                             int l1, uint64_t swapped) {
+  constexpr int F = 2;
+  cp_async_wait_all();
+  for (int l = l0; l < l1; ++l) {
+    float acc[F] = {0.f, 0.f};
+    if (valid) {
+      uint32_t b_;
+      float fx, fy, fz;
+      lattice(m.x, lv.N[l], b_, fx);
+      lattice(m.y, lv.N[l], b_, fy);
+      lattice(m.z, lv.N[l], b_, fz);
+      const int r = l - l0;
+      const uint8_t* lvl = r < cap_a ? stage_a + (uint32_t)r * kStageLevelBytes
+                                     : stage_b + (uint32_t)(r - cap_a) * kStageLevelBytes;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint2 raw = *reinterpret_cast<const uint2*>(lvl + ((uint32_t)q * 128u + s) * 8u);
+        const bool sw = (swapped >> (4 * r + q)) & 1ull;
+        const uint32_t c0 = sw ? raw.y : raw.x, c1 = sw ? raw.x : raw.y;  // corners x, x + 1
+        const float2 v0 = __half22float2(*reinterpret_cast<const __half2*>(&c0));
+        const float2 v1 = __half22float2(*reinterpret_cast<const __half2*>(&c1));
+        // the weights and the order of the sums of encode_to_tile, so both
+        // give the same encoding bit for bit
+        const float wy = (q & 1) ? fy : 1.f - fy, wz = (q >> 1) ? fz : 1.f - fz;
+        const float w0 = ((1.f - fx) * wy) * wz, w1 = (fx * wy) * wz;
+        acc[0] += w0 * v0.x;
+        acc[1] += w0 * v0.y;
+        acc[0] += w1 * v1.x;
+        acc[1] += w1 * v1.y;
+      }
+    }
+    st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
+  }
+}
+
 __device__ __forceinline__ void encode_to_tile_staged(const LevelTab& lv, const __half* __restrict__ tab16,
                                                       uint3 m, bool valid, uint8_t* act, uint32_t s,
                                                       uint8_t* stage_a, int cap_a, uint8_t* stage_b,
                                                       int cap_b) {
-  constexpr int F = 2;
-  const int cap = cap_a + cap_b;
+  // at most 16 levels per round: the swap bits of a round fit 64 bits
+  const int cap = min(cap_a + cap_b, 16);
   for (int l0 = 0; l0 < lv.L; l0 += cap) {
     const int l1 = min(lv.L, l0 + cap);
-    uint64_t swapped = 0;  // bit 4 (l - l0) + q: the pair arrived as (x + 1, x)
-    if (valid) {
-      for (int l = l0; l < l1; ++l) {
-        uint32_t bx, by, bz;
-        float f_;
-        lattice(m.x, lv.N[l], bx, f_);
-        lattice(m.y, lv.N[l], by, f_);
-        lattice(m.z, lv.N[l], bz, f_);
-        const int r = l - l0;
-        const uint32_t lvl = umma::smem_u32(r < cap_a ? stage_a + (uint32_t)r * kStageLevelBytes
-                                                      : stage_b + (uint32_t)(r - cap_a) * kStageLevelBytes);
-        const __half* tab = tab16 + lv.off[l];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint32_t y = by + (q & 1), z = bz + (q >> 1);
-          const uint32_t i0 = corner_index(lv, l, bx, y, z);
-          const uint32_t i1 = corner_index(lv, l, bx + 1, y, z);
-          const uint32_t dst = lvl + ((uint32_t)q * 128u + s) * 8u;
-          if (i1 == (i0 ^ 1u)) {
-            cp_async8(dst, tab + (size_t)(i0 & ~1u) * F);
-            if (i0 & 1u) swapped |= 1ull << (4 * r + q);
-          } else {
-            cp_async4(dst, tab + (size_t)i0 * F);
-            cp_async4(dst + 4u, tab + (size_t)i1 * F);
-          }
-        }
-      }
-    }
-    cp_async_wait_all();
-    for (int l = l0; l < l1; ++l) {
-      float acc[F] = {0.f, 0.f};
-      if (valid) {
-        uint32_t b_;
-        float fx, fy, fz;
-        lattice(m.x, lv.N[l], b_, fx);
-        lattice(m.y, lv.N[l], b_, fy);
-        lattice(m.z, lv.N[l], b_, fz);
-        const int r = l - l0;
-        const uint8_t* lvl = r < cap_a ? stage_a + (uint32_t)r * kStageLevelBytes
-                                       : stage_b + (uint32_t)(r - cap_a) * kStageLevelBytes;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const uint2 raw = *reinterpret_cast<const uint2*>(lvl + ((uint32_t)q * 128u + s) * 8u);
-          const bool sw = (swapped >> (4 * r + q)) & 1ull;
-          const uint32_t c0 = sw ? raw.y : raw.x, c1 = sw ? raw.x : raw.y;  // corners x, x + 1
-          const float2 v0 = __half22float2(*reinterpret_cast<const __half2*>(&c0));
-          const float2 v1 = __half22float2(*reinterpret_cast<const __half2*>(&c1));
-          // the weights and the order of the sums of encode_to_tile, so both
-          // give the same encoding bit for bit
-          const float wy = (q & 1) ? fy : 1.f - fy, wz = (q >> 1) ? fz : 1.f - fz;
-          const float w0 = ((1.f - fx) * wy) * wz, w1 = (fx * wy) * wz;
-          acc[0] += w0 * v0.x;
-          acc[1] += w0 * v0.y;
-          acc[0] += w1 * v1.x;
-          acc[1] += w1 * v1.y;
-        }
-      }
-      st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
-    }
+    const uint64_t swapped = stage_round(lv, tab16, m, valid, s, stage_a, cap_a, stage_b, l0, l1);
+    finish_round(lv, m, valid, act, s, stage_a, cap_a, stage_b, l0, l1, swapped);
   }
 }
 

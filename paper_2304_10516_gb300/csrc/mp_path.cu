@@ -62,7 +62,7 @@ std::atomic<long long> g_first_wait{kWaitCycles};
 
 // Revision of the training kernel's memory behaviour; the DRAM-traffic figure
 // of an Nsight Compute capture is reported only while it matches.
-[[maybe_unused]] constexpr int kTrainKernelRevision = 11;
+[[maybe_unused]] constexpr int kTrainKernelRevision = 12;
 
 struct MpModel {
   const __half* theta16;
@@ -1118,14 +1118,14 @@ int64_t interleaved_launches(const MpParams& q, int n) {
 // Launch-shape autotuner of the grouped training step: on the first call
 // for a configuration (encoding, MLP, batch, number of models) it times a
 // whole step for each candidate -- CTAs per SM (as many as fit, or one),
-// models per wave (the heuristic, half, double) or grid rounds per wave,
-// and the step's layout (training launch then Adam, or interleaved per wave
-// when no schedule is needed) -- on the call's own models and volumes, with
-// Adam in its dry mode (the same traffic, values written back unchanged),
-// then clears what the trials wrote (weight gradients, loss sums, overflow
-// flags; parameters, moments and step counters are not touched) and caches
-// the fastest choice for the process. DVNR_AUTOTUNE=0 keeps the heuristic;
-// DVNR_WAVE_MODELS fixes the wave size; DVNR_INTERLEAVE=0/1 fixes the layout.
+// models per wave (the heuristic, half, double) or grid rounds per wave --
+// in the step's layout (training launch then Adam; interleaved per wave
+// with DVNR_INTERLEAVE=1) on the call's own models and volumes, with Adam
+// in its dry mode (the same traffic, values written back unchanged), then
+// clears what the trials wrote (weight gradients, loss sums, overflow flags;
+// parameters, moments and step counters are not touched) and caches the
+// fastest choice for the process. DVNR_AUTOTUNE=0 keeps the heuristic;
+// DVNR_WAVE_MODELS fixes the wave size.
 struct TuneChoice {
   int ctas_per_sm;
   int64_t wave_tiles;
@@ -1155,11 +1155,11 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, con
       bool dup = false;
       for (const auto& c : cands) dup |= c.ctas_per_sm == ctas && c.wave_tiles == wt;
       if (dup) continue;
-      for (int il = 0; il < 2; ++il) {
-        if (il && base.sched) continue;  // interleaving needs every model in every step
-        if (interleave_env >= 0 && il != interleave_env) continue;
-        cands.push_back({ctas, wt, il != 0});
-      }
+      // the interleaved layout is a candidate only when asked for
+      // (DVNR_INTERLEAVE=1): measured slower on both workloads, its trials
+      // would only lengthen the first call
+      const bool il = interleave_env == 1 && !base.sched;  // needs every model in every step
+      cands.push_back({ctas, wt, il});
     }
     if (ctas == 1) break;
   }
@@ -1443,7 +1443,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   }
   p.models = c->d_models;
   // step layout: training launch then Adam, or interleaved per wave
-  // (DVNR_INTERLEAVE=0/1 fixes it; else the autotuner picks)
+  // (DVNR_INTERLEAVE=1; measured slower on both workloads)
   int interleave_env = -1;
   if (const char* e = getenv("DVNR_INTERLEAVE")) interleave_env = atoi(e) != 0 ? 1 : 0;
   bool interleaved = false;

@@ -14,6 +14,10 @@ volumes that are not available here (Sec. 5). The stand-ins:
   FFT), normalised to [0, 1] -- the turbulence-like 256^3 workload.
 * ``advected``: the same spectrum advected by a uniform drift with viscous
   decay of the high modes, for in situ time series.
+* ``front``: a thin front across a randomly wrinkled surface (a tanh
+  profile about 1.5 voxels thick) over a gentle background, normalised to
+  [0, 1] -- a field with a sharp, localised feature, the kind the paper's
+  combustion fields have and the spectral field lacks.
 * ``uneven_boxes``: a rectangular decomposition into blocks of uneven edge
   (Sec. 3.1 assumes one box per rank), with a ghost layer (Sec. 3.3).
 """
@@ -36,6 +40,28 @@ def blobs(n: int = 64, seed: int = 1001, n_blobs: int = 8) -> np.ndarray:
         f += a[i] * np.exp(-r2 / (2 * s[i] ** 2))
     f = (f - f.min()) / (f.max() - f.min())
     return f.astype(np.float32)
+
+
+def front(shape=(256, 256, 256), seed=1006, width=1.5, modes=6) -> np.ndarray:
+    """(nz, ny, nx) float32 indexed [z, y, x]: 0.5 + 0.5 tanh((z - h(x, y)) /
+    width) with h a random-phase sum of modes (kx, ky) in [1, modes]^2 of
+    amplitude ~ 1/|k| (total excursion about nz/10 voxels) around nz/2, plus a
+    background 0.15 sin(2 pi x) cos(2 pi y); normalised to [0, 1]."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) / nx
+    y = np.arange(ny) / ny
+    X, Y = np.meshgrid(x, y, indexing="xy")  # (ny, nx)
+    h = np.full((ny, nx), nz / 2.0)
+    amp = nz / 10.0 / modes
+    for kx in range(1, modes + 1):
+        for ky in range(1, modes + 1):
+            a = amp / np.hypot(kx, ky) * rng.uniform(0.5, 1.5)
+            h += a * np.sin(2 * np.pi * (kx * X + ky * Y) + rng.uniform(0, 2 * np.pi))
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
+    f = 0.5 + 0.5 * np.tanh((z - h[None]) / width)
+    f += 0.15 * (np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y))[None]
+    return _normalise(f).astype(np.float32)
 
 
 def _spectral_coeffs(shape, seed, slope):

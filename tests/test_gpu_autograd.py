@@ -221,3 +221,29 @@ def test_fp16_kernels_on_the_binary16_pin_networks(dv, orc, A, k, S):
     np.testing.assert_array_equal(dx0.cpu().numpy()[0], r["dx0"][0])
     np.testing.assert_array_equal(g.cpu().numpy(), np.concatenate([r["grad_enc"], r["grad_mlp"]]))
     m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_encode_mlp_trains_under_a_torch_optimizer(dv, A, prec):
+    # EncodeMLP as a building block: a torch optimizer fits the network to a
+    # smooth target through the library's forward and backward kernels
+    c = dict(L=8, F=2, log2T=14, base=4, growth=1.5, width=32, hidden=2)
+    m = _model(dv, c, seed=3)
+    precision = A.DVNR_FP16 if prec == "fp16" else A.DVNR_FP32
+    params = m.params_tensor().requires_grad_(True)
+    opt = torch.optim.Adam([params], lr=1e-2)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    losses = []
+    for step in range(150):
+        coords = torch.randint(0, (1 << 24) + 1, (4096, 3), dtype=torch.int32, device="cuda", generator=gen)
+        u = coords.double() / (1 << 24)
+        target = 0.5 + 0.3 * torch.sin(2 * np.pi * u[:, 0]) * torch.cos(2 * np.pi * u[:, 1]) + 0.1 * u[:, 2]
+        y = dv.EncodeMLP.apply(params, coords, m, precision)
+        loss = ((y.double() - target) ** 2).mean()
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        losses.append(float(loss.detach()))
+    assert np.isfinite(losses).all()
+    assert np.mean(losses[-10:]) < 0.05 * np.mean(losses[:5]), (losses[:5], losses[-10:])
+    m.close()

@@ -61,6 +61,8 @@ CONFIGS = {
     "s3d_w16d16h2_f4": dict(L=4, F=4, log2T=11, base=12, growth=2.0, width=16, hidden=2, batch=1500),
     # width 10: padded to 16, and its layer-0 gradient rows are not 16-byte aligned
     "w32d10h2_f2": dict(L=5, F=2, log2T=12, base=8, growth=1.5, width=32, hidden=2, batch=1200),
+    # more than 16 levels of two features: the staged gathers take two rounds
+    "w64d48h3_l24": dict(L=24, F=2, log2T=14, base=4, growth=1.2, width=64, hidden=3, batch=2048),
 }
 
 
@@ -308,3 +310,39 @@ def test_fp16_error_against_plain_fp64_oracle(dv, orc, A, name):
     ref = orc.decode_grid(oc, th64, (40, 40, 40), 0, 0.0, 1.0)
     assert np.abs(dec - ref).max() <= 2e-3 * (ref.max() - ref.min())
     m.close()
+
+
+def test_interleaved_steps_train_like_plain_steps(dv, A, monkeypatch):
+    # DVNR_INTERLEAVE=1 runs a step wave by wave with each wave's Adam update
+    # before its training launch (here one model per wave); per model the
+    # sequence of operations is that of the plain layout, so the counters
+    # agree exactly and the models reach the same PSNR (up to the reordering
+    # of atomic sums)
+    from paper_2304_10516_gb300 import volumes
+
+    c = dict(P.configs_blobs64(), batch=2048)
+    vols = [torch.from_numpy(volumes.blobs(32, seed=2100 + i)).cuda() for i in range(4)]
+
+    def run(interleave):
+        if interleave:
+            monkeypatch.setenv("DVNR_INTERLEAVE", "1")
+        else:
+            monkeypatch.delenv("DVNR_INTERLEAVE", raising=False)
+        monkeypatch.setenv("DVNR_WAVE_MODELS", "1")
+        ms = [_model(dv, c, seed=60 + i, hi=(32, 32, 32)) for i in range(4)]
+        losses = dv.train(ms, vols, dv.TrainConfig(batch=2048, steps=20, lr=1e-3, seed=9,
+                                                  loss=A.DVNR_LOSS_L2, precision=A.DVNR_FP16))
+        out = []
+        for m, v in zip(ms, vols):
+            st = m.state()
+            sse, _ = dv.error_stats(m.decode_grid(), v)
+            out.append((st["adam_t"], st["iter"], st["skipped"], P.psnr(sse / v.numel())))
+            m.close()
+        return out, losses
+
+    plain, lp = run(False)
+    inter, li = run(True)
+    for (a, b) in zip(plain, inter):
+        assert a[:3] == b[:3] == (20, 20, 0)
+        assert abs(a[3] - b[3]) < 0.05, (a, b)
+    np.testing.assert_allclose(li, lp, rtol=2e-3)
