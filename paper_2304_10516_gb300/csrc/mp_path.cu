@@ -739,6 +739,9 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
           for (int j = 0; j < 16; ++j) h[u * 16 + j] = v[j];
         }
         umma::ld_wait();
+        // ReLU on the binary16 pairs: max(fp16(x), 0) is fp16(max(x, 0)) for
+        // every x (a zero may change sign, which no sum or product here sees)
+        const __half2 zero2 = __float2half2_rn(0.f);
         if (!last) {
 #pragma unroll
           for (int g = 0; g < CH / 8; ++g) {
@@ -746,14 +749,18 @@ __global__ void __launch_bounds__(kTile, F <= 2 ? kDecodeCtasPerSm : 1) k_mp_dec
             uint32_t* pu = &u.x;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-              __half2 q = __floats2half2_rn(fmaxf(h[g * 8 + 2 * j], 0.f), fmaxf(h[g * 8 + 2 * j + 1], 0.f));
+              __half2 q = __hmax2(__floats2half2_rn(h[g * 8 + 2 * j], h[g * 8 + 2 * j + 1]), zero2);
               pu[j] = *reinterpret_cast<uint32_t*>(&q);
             }
             *reinterpret_cast<uint4*>(s_act + tile_off(f0 + c * CH + g * 8, tid)) = u;
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < CH; ++j) y += __half2float(__float2half_rn(fmaxf(h[j], 0.f))) * s_wout[c * CH + j];
+          for (int j = 0; j < CH; j += 2) {
+            const float2 r = __half22float2(__hmax2(__floats2half2_rn(h[j], h[j + 1]), zero2));
+            y += r.x * s_wout[c * CH + j];
+            y += r.y * s_wout[c * CH + j + 1];
+          }
         }
       }
       if (!last) umma::fence_proxy_async();
