@@ -477,7 +477,7 @@ dvnr_status dvnr_error_stats(const float* a_dev, const float* b_dev, int64_t n,
  *    with a message, before any device work.
  *  - The scratch address is looked up once per device, by dvnr_create on its
  *    device or else by the first call on a device (the device must be
- *    current); make that first call before any stream capture.
+ *    current).
  *  - All calls share the scratch array and leave their partial sums in it;
  *    calls whose kernels overlap on the GPU (e.g. on two streams) race and
  *    must be serialised by the caller.
