@@ -519,6 +519,20 @@ int64_t dvnr_launch_count(void);
  * counts one launch per call. Host counters, no synchronisation.           */
 dvnr_status dvnr_graph_stats(int64_t* captures, int64_t* replays, int64_t* eager_steps);
 
+/* Launches of the two FP16 training kernels enqueued by the host since the
+ * library was loaded (each pointer may be NULL): `plain`, the kernel whose
+ * 128 threads per CTA alternate gathers, tensor-core products and
+ * reductions (two CTAs per SM); `ws`, the warp-specialised kernel whose CTA
+ * (one per SM) runs the tensor-core chain on four warps while two groups of
+ * four gather and reduce alternate tiles. A launch
+ * made during graph capture counts once, its replays not at all. Calls use
+ * the plain kernel unless the environment variable DVNR_TRAIN_WS=1 selects
+ * the warp-specialised one wherever its layout fits (two features per
+ * level, an encoding of at most 64 values, 227 KB of shared memory and 512
+ * TMEM columns), including the single-step calls dvnr_train_grad and
+ * dvnr_backward. Host counters, no synchronisation.                      */
+dvnr_status dvnr_train_kernel_stats(int64_t* plain, int64_t* ws);
+
 /* Diagnostic for tests of the failure path: the limit, in SM clocks, of the
  * first tensor-core wait of every CTA of the FP16 training and decoding
  * kernels (later waits keep theirs, about 2 s). cycles >= 0 sets it; 0 gives

@@ -32,7 +32,8 @@ EXPORTS = [
     "dvnr_adaptive_encoding", "dvnr_freeze", "dvnr_window_create", "dvnr_window_destroy",
     "dvnr_window_push", "dvnr_window_range", "dvnr_window_model", "dvnr_window_bytes",
     "dvnr_render_in_frame", "dvnr_composite", "dvnr_set_value_range", "dvnr_adam_step",
-    "dvnr_get_moments", "dvnr_debug_first_wait", "dvnr_graph_stats", "dvnr_load_params",
+    "dvnr_get_moments", "dvnr_debug_first_wait", "dvnr_graph_stats", "dvnr_train_kernel_stats",
+    "dvnr_load_params",
     "dvnr_forward", "dvnr_backward", "dvnr_debug_fail_alloc", "dvnr_debug_live_allocs",
     "dvnr_probe_requests",
 ]
@@ -132,6 +133,7 @@ _SIGS = {
     "dvnr_get_moments": ([_P, _P, _P, C.c_int64], C.c_int),
     "dvnr_debug_first_wait": ([C.c_int64, C.POINTER(C.c_int64)], C.c_int),
     "dvnr_graph_stats": ([C.POINTER(C.c_int64)] * 3, C.c_int),
+    "dvnr_train_kernel_stats": ([C.POINTER(C.c_int64)] * 2, C.c_int),
     "dvnr_load_params": ([_P, _P, _P], C.c_int),
     "dvnr_debug_fail_alloc": ([C.c_int64], C.c_int),
     "dvnr_probe_requests": ([_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P], C.c_int),

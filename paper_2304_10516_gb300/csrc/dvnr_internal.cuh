@@ -56,6 +56,7 @@ cudaError_t dev_free_async(void* p, cudaStream_t s);
 void count_graph_capture();
 void count_graph_replay();
 void count_eager_steps(int64_t n);
+void count_train_launch(bool ws);
 // An NVTX range named after a public call, open for the call's duration (a
 // host-side marker for profilers; without an attached tool it costs a
 // branch).

@@ -54,6 +54,16 @@ struct MpLayout {
   uint32_t tmem_cols;
   uint32_t dw_col[kMaxHidden];      // TMEM column of dW_k
   int ctas_per_sm;
+  // warp-specialised training kernel (k_mp_train_ws): two X0 tiles (ACT's
+  // feature 0 is slot 0's; the hidden activations follow both slots), the
+  // targets (2 x 128 floats) and fixed-point coordinates (2 x 128 x 3) of the
+  // tiles in the slots, the gather staging of each of its two gathering
+  // groups (stage_levels levels each), and the TMEM columns of each slot's
+  // dL/d(encoding)
+  int32_t ws;
+  uint32_t smem_x0[2], smem_tgt, smem_crd, smem_stage;
+  int32_t stage_levels;
+  uint32_t dx_col[2];
 };
 
 // ---------------------------------------------------------------- gathers --
@@ -426,32 +436,38 @@ __device__ __forceinline__ bool scatter_chunk(const LevelTab& lv, float* __restr
 // Load one model's FP16 weights into the core-matrix weight area and w_out
 // (as FP32) into s_wout.
 // W_0 takes lay.dpad input columns, those past D zero.
+// Weights of one model into shared memory, by threads t0 .. t0 + nt - 1 of
+// the block (all of them by default).
 __device__ void load_weights(const __half* __restrict__ theta16, const int64_t* w_off, int D, int H,
-                             int W, const MpLayout& lay, uint8_t* smem) {
+                             int W, const MpLayout& lay, uint8_t* smem, int t0 = -1, int nt = 0) {
+  if (t0 < 0) {
+    t0 = (int)threadIdx.x;
+    nt = (int)blockDim.x;
+  }
   uint8_t* s_w = smem + lay.smem_w;
   float* s_wout = reinterpret_cast<float*>(smem + lay.smem_wout);
   for (int k = 0; k < H; ++k) {
     const int in = k == 0 ? D : W;
     const __half* src = theta16 + w_off[k];
     uint8_t* dst = s_w + lay.wbyte[k];
-    for (int e = threadIdx.x; e < W * in; e += blockDim.x) {
+    for (int e = t0; e < W * in; e += nt) {
       const int o = e / in, i = e - o * in;
       *reinterpret_cast<__half*>(dst + wsm_off(o, i, W)) = src[e];
     }
     if (k == 0) {
-      for (int e = threadIdx.x; e < W * ((int)lay.dpad - D); e += blockDim.x) {
+      for (int e = t0; e < W * ((int)lay.dpad - D); e += nt) {
         const int w = (int)lay.dpad - D, o = e / w, i = D + (e - o * w);
         *reinterpret_cast<__half*>(dst + wsm_off(o, i, W)) = __float2half(0.f);
       }
     }
   }
-  for (int j = threadIdx.x; j < W; j += blockDim.x) s_wout[j] = __half2float(theta16[w_off[H] + j]);
+  for (int j = t0; j < W; j += nt) s_wout[j] = __half2float(theta16[w_off[H] + j]);
 }
 
-// Forward MMA chain of layer k: scratch[0:W) = ACT(k) x W_k^T.
-__device__ __forceinline__ void issue_forward(uint32_t tmem, const uint8_t* smem, const MpLayout& lay,
-                                              int k, int in, int W) {
-  const uint32_t a0 = umma::smem_u32(smem + lay.smem_act) + (lay.act_off[k] >> 3) * 2048u;
+// Forward MMA chain of layer k: scratch[0:W) = A x W_k^T, A the tile at
+// shared address a0 (in features).
+__device__ __forceinline__ void issue_forward_at(uint32_t tmem, uint32_t a0, const uint8_t* smem,
+                                                 const MpLayout& lay, int k, int in, int W) {
   const uint32_t b0 = umma::smem_u32(smem + lay.smem_w + lay.wbyte[k]);
   const uint32_t id = umma::idesc_f16(kTile, W, 0, 0);
   const uint32_t wb = (uint32_t)(W >> 3) * 128u;
@@ -460,6 +476,12 @@ __device__ __forceinline__ void issue_forward(uint32_t tmem, const uint8_t* smem
     const uint64_t b = umma::sdesc(b0 + kk * 2u * wb, wb, 128u);
     umma::mma_f16(tmem, a, b, id, kk > 0);
   }
+}
+// ... with A = ACT(k).
+__device__ __forceinline__ void issue_forward(uint32_t tmem, const uint8_t* smem, const MpLayout& lay,
+                                              int k, int in, int W) {
+  issue_forward_at(tmem, umma::smem_u32(smem + lay.smem_act) + (lay.act_off[k] >> 3) * 2048u, smem, lay, k,
+                   in, W);
 }
 
 
@@ -490,6 +512,11 @@ int sm_count() {
   }
   return n;
 }
+
+// Layout of k_mp_train_ws (F = 2, encodings of at most 64 features, one
+// CTA per SM): false when the configuration exceeds 227 KB of shared memory
+// or 512 TMEM columns.
+bool make_layout_ws(const dvnr_model m, MpLayout& lay);
 
 uint32_t pow2_cols(uint32_t c) {
   uint32_t p2 = 32;
@@ -552,6 +579,65 @@ bool make_layout(const dvnr_model m, bool train, MpLayout& lay) {
   const int by_tmem = (int)(512 / lay.tmem_cols);
   lay.ctas_per_sm = std::max(1, std::min(std::min(by_smem, by_tmem), train ? 2 : kDecodeCtasPerSm));
   return true;
+}
+
+bool make_layout_ws(const dvnr_model m, MpLayout& lay) {
+  const int W = m->mlp.width, H = m->mlp.n_hidden;
+  const int D = (m->lv.in_dim + 15) / 16 * 16;
+  lay = MpLayout{};
+  if (m->lv.F != 2 || D > 64) return false;
+  lay.ws = 1;
+  lay.dpad = (uint32_t)D;
+  // mbarriers (tensor core, slot full x2, dL/dX0 ready x2, dL/dX0 read x2,
+  // teardown), TMEM slot, abort flag, the gathering threads' current model
+  uint32_t off = 128;
+  lay.smem_wout = off;
+  off += 64 * 4;
+  off = (off + 127) / 128 * 128;
+  lay.smem_w = off;
+  uint32_t wb = 0;
+  for (int k = 0; k < H; ++k) {
+    lay.wbyte[k] = wb;
+    wb += (uint32_t)W * (k == 0 ? D : W) * 2;
+  }
+  off += wb;
+  off = (off + 1023) / 1024 * 1024;
+  const uint32_t feat_bytes = 2048 / 8;
+  lay.smem_dz = off;
+  off += (uint32_t)H * W * feat_bytes;
+  lay.smem_act = off;
+  lay.smem_x0[0] = off;
+  lay.smem_x0[1] = off + (uint32_t)D * feat_bytes;
+  lay.act_off[0] = 0;
+  for (int k = 1; k < H; ++k) lay.act_off[k] = 2u * (uint32_t)D + (uint32_t)(k - 1) * W;
+  off += (2u * (uint32_t)D + (uint32_t)(H - 1) * W) * feat_bytes;
+  // the weight-gradient product of dZ_H reads 128 features from its start
+  // (rows past W land in TMEM lanes that are never read)
+  off = std::max(off, lay.smem_dz + ((uint32_t)(H - 1) * W + 128) * feat_bytes);
+  lay.smem_tgt = off;
+  off += 2 * 128 * 4;
+  lay.smem_crd = off;
+  off += 2 * 128 * 12;
+  off = (off + 1023) / 1024 * 1024;
+  // the two gathering groups' staging areas, as many levels per round as fit
+  lay.smem_stage = off;
+  const int fit = (int)(((227u * 1024u > off) ? 227u * 1024u - off : 0u) / (2u * kStageLevelBytes));
+  lay.stage_levels = std::min(std::min(m->lv.L, 16), fit);
+  if (lay.stage_levels < 1) return false;
+  off += 2u * (uint32_t)lay.stage_levels * kStageLevelBytes;
+  lay.smem_bytes = (off + 1023) / 1024 * 1024;
+  uint32_t col = (uint32_t)std::max(W, D);
+  for (int k = 0; k < H; ++k) {
+    lay.dw_col[k] = col;
+    col += (uint32_t)(k == 0 ? D : W);
+  }
+  lay.dx_col[0] = col;
+  col += (uint32_t)D;
+  lay.dx_col[1] = col;
+  col += (uint32_t)D;
+  lay.tmem_cols = pow2_cols(col);
+  lay.ctas_per_sm = 1;
+  return lay.tmem_cols <= 512 && lay.smem_bytes <= 227 * 1024;
 }
 
 // CTAs of `kernel` resident per SM at `threads` threads and `smem` bytes of

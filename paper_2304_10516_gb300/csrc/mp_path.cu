@@ -585,6 +585,545 @@ teardown:
   if (warp == 0) umma::tmem_dealloc(tmem, p.lay.tmem_cols);
 }
 
+// ------------------------------------------ warp-specialised training ---
+// k_mp_train_ws: the step of k_mp_train with the memory work and the
+// tensor-core chain on different warps of one CTA per SM. Warps 0-3 (the
+// chain) run the tiles' forward products, loss and backward products in
+// order; two gathering groups (warps 4-7 and 8-11) take alternate tiles: a
+// group gathers its tile into its X0 slot, waits for the chain's products of
+// that tile, then scatters the tile's dL/d(encoding) into the table
+// gradients, so that one group's gathers, the other's reductions and the
+// chain's products overlap. Handoffs are mbarriers: full[b] (128 arrivals: X0
+// slot b, its targets and coordinates written), dx[b] (the chain's commit
+// after a tile's last products: its dL/dX0 is in slot b's TMEM columns and X0
+// slot b is free) and dxfree[b] (128 arrivals: slot b's dL/dX0 read back). Every wait is
+// bounded; a wait that gives up raises the CTA's abort flag, and each warp
+// group leaves its loop at its next group barrier, which takes the OR of its
+// threads' view of the flag so that the group decides as one. Same results
+// as k_mp_train up to the order of the floating-point reductions.
+template <int W, int F>
+__global__ void __launch_bounds__(3 * kTile, 1) k_mp_train_ws(const __grid_constant__ MpParams p) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 8);
+  volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(smem + 12);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 16);    // [2]
+  uint64_t* dxr = reinterpret_cast<uint64_t*>(smem + 32);     // [2]
+  uint64_t* dxfree = reinterpret_cast<uint64_t*>(smem + 48);  // [2]
+  uint64_t* fin = reinterpret_cast<uint64_t*>(smem + 64);
+  volatile int32_t* mem_model = reinterpret_cast<volatile int32_t*>(smem + 72);  // [2]
+  uint8_t* s_act = smem + p.lay.smem_act;
+  uint8_t* s_dz = smem + p.lay.smem_dz;
+  const float* s_wout = reinterpret_cast<const float*>(smem + p.lay.smem_wout);
+  float* s_tgt = reinterpret_cast<float*>(smem + p.lay.smem_tgt);
+  uint32_t* s_crd = reinterpret_cast<uint32_t*>(smem + p.lay.smem_crd);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool chain = tid < kTile;
+  const int lt = tid & (kTile - 1);  // thread within its warp group: TMEM lane and tile sample
+  const int D = p.D, H = p.H;
+  const int n_act = p.sched ? p.sched[0] : p.n_models;
+  if (n_act <= 0) return;
+  const int64_t T_act = (int64_t)n_act * p.tiles_per_model;
+  const int n_waves = (int)((T_act + p.wave_tiles - 1) / p.wave_tiles);
+  const int wv_end = p.wave_end < 0 ? n_waves : min(p.wave_end, n_waves);
+
+  if (tid == 0) {
+    umma::mbar_init(mbar, 1);
+    for (int b = 0; b < 2; ++b) {
+      umma::mbar_init(full + b, kTile);
+      umma::mbar_init(dxr + b, 1);
+      umma::mbar_init(dxfree + b, kTile);
+    }
+    umma::mbar_init(fin, 1);
+    *abort_flag = 0u;
+    mem_model[0] = mem_model[1] = -1;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, p.lay.tmem_cols);
+  // the zero padding of the X0 slots (features D .. dpad-1), each by its
+  // gathering group: nothing else writes it
+  if ((int)p.lay.dpad > D && !chain)
+    zero_pad_rows<F>(D, (int)p.lay.dpad, smem + p.lay.smem_x0[(warp >> 2) - 1], (uint32_t)lt);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's TMEM lanes
+
+  // the CTA's tiles in order: its share of each wave in turn; (wv, g, ge)
+  // advances to the next tile, false when there is none
+  auto next_tile = [&](int& wv, int64_t& g, int64_t& ge) -> bool {
+    ++g;
+    while (g >= ge) {
+      if (++wv >= wv_end) return false;
+      const int64_t wb = (int64_t)wv * p.wave_tiles;
+      const int64_t Tw = p.wave_tiles < T_act - wb ? p.wave_tiles : T_act - wb;
+      g = wb + (Tw * blockIdx.x) / gridDim.x;
+      ge = wb + (Tw * (blockIdx.x + 1)) / gridDim.x;
+    }
+    return true;
+  };
+  auto model_of = [&](int64_t g, int& tile) -> int {
+    const int pos = (int)(g / p.tiles_per_model);
+    tile = (int)(g - (int64_t)pos * p.tiles_per_model);
+    return p.sched ? p.sched[1 + pos] : pos;
+  };
+  auto scale_of = [&](const MpModel& md) -> float {
+    return p.ext_scale ? *p.ext_scale : (p.loss_scale_override > 0.f ? p.loss_scale_override : md.st->loss_scale);
+  };
+
+  int cur = -1;  // the chain's model
+  MpModel md{};
+  if (chain) {
+    // ------------------------------------------------------------ chain --
+    uint32_t phase = 0;
+    long long wait_limit = p.first_wait_cycles;
+    auto mma_wait = [&]() -> bool {
+      umma::mbar_wait_bounded(mbar, phase, abort_flag, wait_limit);
+      wait_limit = kWaitCycles;
+      phase ^= 1u;
+      return !umma::bar_or(1, kTile, *abort_flag != 0u);
+    };
+    auto group_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+      umma::mbar_wait_bounded(bar, parity, abort_flag, kWaitCycles);
+      return !umma::bar_or(1, kTile, *abort_flag != 0u);
+    };
+    bool first_tile = true;
+    float S = 1.f;
+    constexpr int NOUT = W >= 32 ? W / 32 : 1;
+    float acc_out[NOUT];
+    float loss_acc = 0.f;
+    // the run's weight gradients and loss of the current model into the
+    // model's MLP gradient and loss sum, as k_mp_train's flush
+    auto flush = [&]() {
+      umma::fence_after_sync();
+      float* part = md.grad + p.w_off[0];
+      if (warp * 32 < W) {
+        const int r = warp * 32 + lane;
+        for (int k = 0; k < H; ++k) {
+          const int in = k == 0 ? D : W;
+          float* g = part + (p.w_off[k] - p.w_off[0]);
+          for (int c = 0; c < in; c += 16) {
+            float v[16];
+            umma::ld16(tl + p.lay.dw_col[k] + c, v);
+            umma::ld_wait();
+            if (r < W && (in & 15) == 0) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) red_add<4>(g + (size_t)r * in + c + 4 * j, v + 4 * j);
+            } else if (r < W) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const int c0 = c + 4 * j;
+                if (c0 + 4 <= in && (in & 3) == 0) {
+                  red_add<4>(g + (size_t)r * in + c0, v + 4 * j);
+                } else {
+#pragma unroll
+                  for (int e = 0; e < 4; ++e)
+                    if (c0 + e < in) atomicAdd(g + (size_t)r * in + c0 + e, v[4 * j + e]);
+                }
+              }
+            }
+          }
+        }
+      }
+      float* s_red = reinterpret_cast<float*>(s_dz);
+      if (W >= 32) {
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) s_red[warp * (W + 1) + NOUT * lane + j] = acc_out[j];
+      } else if (!(lane & 1)) {
+        s_red[warp * (W + 1) + (lane >> 1)] = acc_out[0];
+      }
+      float l = loss_acc;
+      for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+      if (lane == 0) s_red[warp * (W + 1) + W] = l;
+      umma::bar_sync(1, kTile);
+      if (lt <= W) {
+        const float t = s_red[lt] + s_red[(W + 1) + lt] + s_red[2 * (W + 1) + lt] + s_red[3 * (W + 1) + lt];
+        if (lt < W)
+          atomicAdd(part + (p.w_off[H] - p.w_off[0]) + lt, t);
+        else
+          atomicAdd(&md.st->loss_sum, t);
+      }
+      umma::fence_before_sync();
+      umma::bar_sync(1, kTile);
+    };
+
+    int wv = p.wave_first - 1;
+    int64_t g = 0, ge = 0, t = 0;
+    bool go = true;
+    while (go && next_tile(wv, g, ge)) {
+      const int b = (int)(t & 1);
+      const uint32_t use = (uint32_t)(t >> 1);
+      if (!group_wait(full + b, use & 1u)) break;
+      int tile;
+      const int model = model_of(g, tile);
+      if (model != cur) {
+        if (cur >= 0) {
+          // the previous tile's last products complete before the run's dW leave TMEM
+          if (!group_wait(dxr + ((t - 1) & 1), (uint32_t)((t - 1) >> 1) & 1u)) break;
+          flush();
+        }
+        cur = model;
+        md = p.models[model];
+        S = scale_of(md);
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) acc_out[j] = 0.f;
+        loss_acc = 0.f;
+        first_tile = true;
+        load_weights(md.theta16, p.w_off, D, H, W, p.lay, smem, lt, kTile);
+        umma::fence_proxy_async();
+        umma::fence_before_sync();
+        umma::bar_sync(1, kTile);
+      }
+      const int i = tile * kTile + lt;
+      const bool valid = i < p.batch;
+      const float target = s_tgt[b * kTile + lt];
+      const uint32_t x0 = umma::smem_u32(smem + p.lay.smem_x0[b]);
+
+      // -- forward: H_{k+1} = ReLU(H_k W_k^T)
+      float h[W];
+      uint64_t maskH = 0;
+      for (int k = 0; k < H; ++k) {
+        if (lt == 0) {
+          umma::fence_after_sync();
+          const uint32_t a0 = k == 0 ? x0 : umma::smem_u32(s_act) + (p.lay.act_off[k] >> 3) * 2048u;
+          issue_forward_at(tmem, a0, smem, p.lay, k, k == 0 ? (int)p.lay.dpad : W, W);
+          umma::commit(mbar);
+        }
+        if (!mma_wait()) {
+          go = false;
+          break;
+        }
+        umma::fence_after_sync();
+#pragma unroll
+        for (int c = 0; c < W / 16; ++c) {
+          float v[16];
+          umma::ld16(tl + c * 16, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) h[c * 16 + j] = v[j];
+        }
+        umma::ld_wait();
+        if (k < H - 1) {
+          const uint32_t f0 = p.lay.act_off[k + 1];
+#pragma unroll
+          for (int c = 0; c < W / 8; ++c) {
+            uint4 u;
+            uint32_t* pu = &u.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              __half2 q = __floats2half2_rn(fmaxf(h[c * 8 + 2 * j], 0.f), fmaxf(h[c * 8 + 2 * j + 1], 0.f));
+              pu[j] = *reinterpret_cast<uint32_t*>(&q);
+            }
+            *reinterpret_cast<uint4*>(s_act + tile_off(f0 + c * 8, lt)) = u;
+          }
+          umma::fence_proxy_async();
+        } else {
+#pragma unroll
+          for (int j = 0; j < W; ++j) {
+            if (h[j] > 0.f) maskH |= 1ull << j;
+            h[j] = __half2float(__float2half_rn(fmaxf(h[j], 0.f)));
+          }
+        }
+        umma::fence_before_sync();
+        umma::bar_sync(1, kTile);
+      }
+      if (!go) break;
+
+      {
+        // -- output, loss, dL/dy (scaled by S)
+        float y = 0.f;
+#pragma unroll
+        for (int j = 0; j < W; ++j) y += h[j] * s_wout[j];
+        float dy = 0.f;
+        if (valid && p.ext_dy) {
+          dy = p.ext_dy[i] * S;
+          if (!isfinite(y)) atomicOr(&md.st->overflow, 1u);
+        } else if (valid) {
+          const float d = y - target;
+          if (p.loss == DVNR_LOSS_L1) {
+            loss_acc += fabsf(d);
+            dy = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * (S * p.inv_batch);
+          } else {
+            loss_acc += d * d;
+            dy = 2.f * d * (S * p.inv_batch);
+          }
+          if (!isfinite(y)) atomicOr(&md.st->overflow, 1u);
+          if (p.dbg_y && cur == 0) {
+            p.dbg_y[i] = y;
+            p.dbg_tgt[i] = target;
+            const uint32_t* crd = s_crd + 3 * (b * kTile + lt);
+            p.dbg_coords[3 * i] = crd[0];
+            p.dbg_coords[3 * i + 1] = crd[1];
+            p.dbg_coords[3 * i + 2] = crd[2];
+          }
+        }
+        // dW_out += fp16(dy) h_H, reduced over the warp (reduce-scatter)
+        {
+          const float dy16 = __half2float(__float2half_rn(dy));
+          float v[W];
+#pragma unroll
+          for (int j = 0; j < W; ++j) v[j] = dy16 * h[j];
+          int n = W;
+#pragma unroll
+          for (int s = 16; s >= 1; s >>= 1) {
+            if (n > 1) {
+              const bool upper = (lane & s) != 0;
+              const int half = n / 2;
+#pragma unroll
+              for (int j = 0; j < W / 2; ++j) {
+                if (j < half) {
+                  const float send = upper ? v[j] : v[j + half];
+                  const float keep = upper ? v[j + half] : v[j];
+                  v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+                }
+              }
+              n = half;
+            } else {
+              v[0] += __shfl_xor_sync(0xffffffffu, v[0], s);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < NOUT; ++j) acc_out[j] += v[j];
+        }
+        // dZ_H = fp16(dy w_out) where z_H > 0
+        const uint32_t f0 = (uint32_t)(H - 1) * W;
+#pragma unroll
+        for (int c = 0; c < W / 8; ++c) {
+          uint4 u;
+          uint32_t* pu = &u.x;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int a = c * 8 + 2 * j;
+            const float v0 = ((maskH >> a) & 1ull) ? dy * s_wout[a] : 0.f;
+            const float v1 = ((maskH >> (a + 1)) & 1ull) ? dy * s_wout[a + 1] : 0.f;
+            __half2 q = __floats2half2_rn(v0, v1);
+            pu[j] = *reinterpret_cast<uint32_t*>(&q);
+          }
+          *reinterpret_cast<uint4*>(s_dz + tile_off(f0 + c * 8, lt)) = u;
+        }
+      }
+      umma::fence_proxy_async();
+      umma::fence_before_sync();
+      umma::bar_sync(1, kTile);
+
+      // -- backward through layers H .. 2: layer k maps H_{k-1} -> Z_k with W_{k-1}
+      for (int k = H; k >= 2; --k) {
+        if (lt == 0) {
+          umma::fence_after_sync();
+          const uint32_t dz0 = umma::smem_u32(s_dz) + ((uint32_t)((k - 1) * W) >> 3) * 2048u;
+          const uint32_t act0 = umma::smem_u32(s_act) + (p.lay.act_off[k - 1] >> 3) * 2048u;
+          // dW_{k-1} += dZ_k^T H_{k-1} (K = samples; both operands MN-major)
+          const uint32_t idw = umma::idesc_f16(kTile, W, 1, 1);
+          for (int ks = 0; ks < kTile / 16; ++ks) {
+            const uint64_t a = umma::sdesc(dz0 + ks * 256u, 128u, 2048u);
+            const uint64_t bb = umma::sdesc(act0 + ks * 256u, 128u, 2048u);
+            umma::mma_f16(tmem + p.lay.dw_col[k - 1], a, bb, idw, (first_tile && ks == 0) ? 0u : 1u);
+          }
+          // dH_{k-1} = dZ_k W_{k-1} (A K-major over the W outputs, B MN-major)
+          const uint32_t ibw = umma::idesc_f16(kTile, W, 0, 1);
+          const uint32_t w0 = umma::smem_u32(smem + p.lay.smem_w + p.lay.wbyte[k - 1]);
+          const uint32_t wb = (uint32_t)(W >> 3) * 128u;
+          for (int kk = 0; kk < W / 16; ++kk) {
+            const uint64_t a = umma::sdesc(dz0 + kk * 4096u, 2048u, 128u);
+            const uint64_t bb = umma::sdesc(w0 + kk * 256u, 128u, wb);
+            umma::mma_f16(tmem, a, bb, ibw, kk > 0);
+          }
+          umma::commit(mbar);
+        }
+        if (!mma_wait()) {
+          go = false;
+          break;
+        }
+        umma::fence_after_sync();
+        float dh[W];
+#pragma unroll
+        for (int c = 0; c < W / 16; ++c) {
+          float v[16];
+          umma::ld16(tl + c * 16, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) dh[c * 16 + j] = v[j];
+        }
+        umma::ld_wait();
+        const uint32_t fa = p.lay.act_off[k - 1], fz = (uint32_t)(k - 2) * W;
+#pragma unroll
+        for (int c = 0; c < W / 8; ++c) {
+          const uint4 hv = *reinterpret_cast<const uint4*>(s_act + tile_off(fa + c * 8, lt));
+          const uint32_t* ph = &hv.x;
+          uint4 u;
+          uint32_t* pu = &u.x;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const __half2 hh = *reinterpret_cast<const __half2*>(ph + j);
+            const float2 hf = __half22float2(hh);
+            const float v0 = hf.x > 0.f ? dh[c * 8 + 2 * j] : 0.f;
+            const float v1 = hf.y > 0.f ? dh[c * 8 + 2 * j + 1] : 0.f;
+            __half2 q = __floats2half2_rn(v0, v1);
+            pu[j] = *reinterpret_cast<uint32_t*>(&q);
+          }
+          *reinterpret_cast<uint4*>(s_dz + tile_off(fz + c * 8, lt)) = u;
+        }
+        umma::fence_proxy_async();
+        umma::fence_before_sync();
+        umma::bar_sync(1, kTile);
+      }
+      if (!go) break;
+      // -- layer 1: dW_0 += dZ_1^T X0 and dL/dX0 = dZ_1 W_0 into slot b's
+      // columns, once the gathering warps have read the slot's previous
+      // dL/dX0; the commit on dx[b] hands both the gradient and the free X0
+      // slot to them (no wait here: the next tile's products queue behind)
+      if (lt == 0) {
+        bool ok = true;
+        if (t >= 2) ok = umma::mbar_wait_bounded(dxfree + b, (use - 1u) & 1u, abort_flag, kWaitCycles);
+        if (ok) {
+          umma::fence_after_sync();
+          const uint32_t dz0 = umma::smem_u32(s_dz);
+          const int in = (int)p.lay.dpad;  // layer 0's K includes the zero padding
+          const uint32_t idw = umma::idesc_f16(kTile, in, 1, 1);
+          for (int ks = 0; ks < kTile / 16; ++ks) {
+            const uint64_t a = umma::sdesc(dz0 + ks * 256u, 128u, 2048u);
+            const uint64_t bb = umma::sdesc(x0 + ks * 256u, 128u, 2048u);
+            umma::mma_f16(tmem + p.lay.dw_col[0], a, bb, idw, (first_tile && ks == 0) ? 0u : 1u);
+          }
+          const uint32_t ibw = umma::idesc_f16(kTile, in, 0, 1);
+          const uint32_t w0 = umma::smem_u32(smem + p.lay.smem_w + p.lay.wbyte[0]);
+          const uint32_t wb = (uint32_t)(W >> 3) * 128u;
+          for (int kk = 0; kk < W / 16; ++kk) {
+            const uint64_t a = umma::sdesc(dz0 + kk * 4096u, 2048u, 128u);
+            const uint64_t bb = umma::sdesc(w0 + kk * 256u, 128u, wb);
+            umma::mma_f16(tmem + p.lay.dx_col[b], a, bb, ibw, kk > 0);
+          }
+          umma::commit(dxr + b);
+        }
+      }
+      first_tile = false;
+      ++t;
+    }
+    // the last tile's products complete before the run's dW leave TMEM
+    if (go && cur >= 0 && t > 0) {
+      if (group_wait(dxr + ((t - 1) & 1), (uint32_t)((t - 1) >> 1) & 1u)) flush();
+    }
+  } else {
+    // -------------------------------------------------- gathering warps --
+    // group gj (warps 4 + 4 gj .. 7 + 4 gj) takes the tiles t = gj, gj + 2,
+    // ... through X0 slot gj and its own staging area
+    const int gj = (warp >> 2) - 1;
+    const uint32_t bar_id = 2u + (uint32_t)gj;
+    uint8_t* stage = smem + p.lay.smem_stage + (uint32_t)gj * (uint32_t)p.lay.stage_levels * kStageLevelBytes;
+    auto group_wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+      umma::mbar_wait_bounded(bar, parity, abort_flag, kWaitCycles);
+      return !umma::bar_or(bar_id, kTile, *abort_flag != 0u);
+    };
+    // sample, target and encoding of tile g into slot b, then the slot's arrival
+    auto gather = [&](int64_t g, int b) -> uint3 {
+      int tile;
+      const int model = model_of(g, tile);
+      const MpModel mg = p.models[model];
+      SampleParams sp;
+      sp.key = p.key;
+      sp.n_bnd = p.n_bnd;
+      sp.qtab = p.qtab;
+      sp.model = mg.slot;
+      const uint32_t iter = p.explicit_iter ? p.iter : mg.st->iter;
+      const int i = tile * kTile + lt;
+      const bool valid = i < p.batch;
+      uint3 mc = make_uint3(0u, 0u, 0u);
+      if (valid)
+        mc = p.ext_coords ? make_uint3(p.ext_coords[3 * i], p.ext_coords[3 * i + 1], p.ext_coords[3 * i + 2])
+                          : draw_sample(sp, (uint32_t)i, iter);
+      VolCorners vc{};
+      if (valid && mg.vol) vc = vol_fetch(mg.vol, mg.nx, mg.ny, mg.nz, mc);  // in flight during the encode
+      encode_to_tile_staged(p.lv, mg.theta16, mc, valid, smem + p.lay.smem_x0[b], (uint32_t)lt, stage,
+                            p.lay.stage_levels, nullptr, 0);
+      float vmin, inv_range;
+      value_range(mg.st, vmin, inv_range);
+      s_tgt[b * kTile + lt] = (valid && mg.vol) ? (vol_interp(vc) - vmin) * inv_range : 0.f;
+      uint32_t* crd = s_crd + 3 * (b * kTile + lt);
+      crd[0] = mc.x;
+      crd[1] = mc.y;
+      crd[2] = mc.z;
+      umma::fence_proxy_async();
+      umma::mbar_arrive(full + b);
+      return mc;
+    };
+    int wv = p.wave_first - 1;
+    int64_t g = 0, ge = 0, t = 0;
+    while (next_tile(wv, g, ge)) {
+      if ((int)(t & 1) != gj) {  // the other group's tile
+        ++t;
+        continue;
+      }
+      const int b = gj;
+      const uint3 mc = gather(g, b);
+      // tile t's dL/dX0 (its products complete, and with them every read of
+      // X0 slot b), read back 16 columns at a time and reduced into the
+      // table gradients
+      if (!group_wait(dxr + b, (uint32_t)(t >> 1) & 1u)) break;
+      umma::fence_after_sync();
+      int tile;
+      const int model = model_of(g, tile);
+      if (lt == 0) mem_model[gj] = model;
+      const MpModel ms = p.models[model];
+      const int i = tile * kTile + lt;
+      const bool valid = i < p.batch;
+      const float inv_S = 1.0f / scale_of(ms);
+      float* dbg_row = (p.dbg_dx0 && model == 0 && valid) ? p.dbg_dx0 + (size_t)i * D : nullptr;
+      bool bad = false;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c * 16 >= D) break;
+        float d[16];
+        umma::ld16(tl + p.lay.dx_col[b] + (uint32_t)(c * 16), d);
+        umma::ld_wait();
+        if (!valid) continue;
+        if (dbg_row) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c * 16 + j < D) dbg_row[c * 16 + j] = d[j] * inv_S;
+        }
+        if (c * 16 + 16 <= D)
+          bad |= scatter_chunk<F, false>(p.lv, ms.grad, mc, d, c * 16);
+        else
+          bad |= scatter_chunk<F, true>(p.lv, ms.grad, mc, d, c * 16);
+      }
+      if (bad) atomicOr(&ms.st->overflow, 1u);
+      // slot b's dL/dX0 has been read: the chain may overwrite it
+      umma::fence_before_sync();
+      umma::mbar_arrive(dxfree + b);
+      umma::bar_sync(bar_id, kTile);
+      if (lt == 0) mem_model[gj] = -1;
+      ++t;
+    }
+  }
+
+  // -- teardown (both groups have left their loops)
+  umma::fence_before_sync();
+  __syncthreads();
+  if (*abort_flag && tid == 0) {
+    // every product this thread issued completes (bounded) before TMEM is freed
+    umma::commit(fin);
+    const long long t0 = clock64();
+    while (!umma::mbar_try_wait(fin, 0u) && clock64() - t0 < kWaitCycles) {
+    }
+    // the steps of the models whose gradients are incomplete: count the
+    // timeout and have Adam skip them (kStepAborted clears the gradient)
+    if (cur >= 0) {
+      atomicAdd(&md.st->timeouts, 1u);
+      atomicOr(&md.st->overflow, kStepAborted);
+    }
+    for (int j = 0; j < 2; ++j) {
+      const int mm = mem_model[j];
+      if (mm >= 0 && mm != cur && (j == 0 || mm != mem_model[0])) {
+        const MpModel mx = p.models[mm];
+        atomicAdd(&mx.st->timeouts, 1u);
+        atomicOr(&mx.st->overflow, kStepAborted);
+      }
+    }
+  }
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(tmem, p.lay.tmem_cols);
+}
+
 // The step's active models in index order (a block-wide exclusive scan of
 // model_active over the models): sched[0] = count, sched[1 + a] = index of the
 // a-th active model, sched[1 + n + m] = position of model m or -1. One block
@@ -896,6 +1435,11 @@ void set_smem_attr(bool train, uint32_t bytes) {
     cudaFuncSetAttribute(k_mp_train<W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     cudaFuncSetAttribute(k_mp_train<W, F>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
+    if constexpr (F == 2) {
+      cudaFuncSetAttribute(k_mp_train_ws<W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+      cudaFuncSetAttribute(k_mp_train_ws<W, F>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+    }
   } else {
     cudaFuncSetAttribute(k_mp_decode<W, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     cudaFuncSetAttribute(k_mp_decode<W, F>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -905,6 +1449,14 @@ void set_smem_attr(bool train, uint32_t bytes) {
 
 template <int W, int F>
 void launch_train_wf(const MpParams& p, int grid, cudaStream_t s) {
+  if constexpr (F == 2) {
+    if (p.lay.ws) {
+      count_train_launch(true);
+      k_mp_train_ws<W, F><<<grid, 3 * kTile, p.lay.smem_bytes, s>>>(p);
+      return;
+    }
+  }
+  count_train_launch(false);
   k_mp_train<W, F><<<grid, kTile, p.lay.smem_bytes, s>>>(p);
 }
 template <int W, int F>
@@ -939,6 +1491,7 @@ struct MpCache {
   int ctas_per_sm = 0;
   bool scheduled = false;  // the captured graph launches k_mp_schedule
   bool interleaved = false;  // the captured steps interleave Adam per wave
+  bool ws = false;           // the captured steps launch k_mp_train_ws
   // early-stop graph: arm node -> WHILE { steps, k_mp_continue }
   bool looped = false;          // exec holds the loop graph
   bool loop_unavailable = false;  // building it failed once: fixed graphs only
@@ -1137,9 +1690,18 @@ struct TuneChoice {
   int ctas_per_sm;
   int64_t wave_tiles;
   bool interleaved;
+  bool ws;  // the warp-specialised kernel (k_mp_train_ws)
 };
 std::mutex g_tune_mu;
 std::map<std::string, TuneChoice> g_tune;
+
+// DVNR_TRAIN_WS: 1 selects k_mp_train_ws wherever its layout fits (unset: -1,
+// and 0: k_mp_train).
+int train_ws_env() {
+  const char* e = getenv("DVNR_TRAIN_WS");
+  if (!e) return -1;
+  return atoi(e) != 0 ? 1 : 0;
+}
 
 std::string tune_key(const dvnr_model m, int n, const dvnr_train_cfg* cfg) {
   char buf[256];
@@ -1150,27 +1712,38 @@ std::string tune_key(const dvnr_model m, int n, const dvnr_train_cfg* cfg) {
 }
 
 dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, const AdamModelPtrs* d_adam,
-                     const AdamHyper& h, int interleave_env, TuneChoice* out, cudaStream_t s) {
+                     const AdamHyper& h, int interleave_env, const MpLayout* lay_ws, bool only_ws,
+                     TuneChoice* out, cudaStream_t s) {
   std::vector<TuneChoice> cands;
-  for (int ctas = base.lay.ctas_per_sm; ctas >= 1; ctas = ctas > 1 ? 1 : 0) {
-    MpParams q = base;
-    q.lay.ctas_per_sm = ctas;
+  auto add = [&](const MpParams& q, int ctas, bool ws) {
     const int hq = heuristic_models_per_wave(q, models[0], n);
     const int64_t G = train_grid(q), tpm = q.tiles_per_model, T = q.total_tiles;
     for (int64_t wt : {hq * tpm, std::max(1, hq / 2) * tpm, std::min(n, 2 * hq) * tpm, G, 2 * G, 4 * G, T}) {
       wt = std::max<int64_t>(1, std::min(wt, T));
       bool dup = false;
-      for (const auto& c : cands) dup |= c.ctas_per_sm == ctas && c.wave_tiles == wt;
+      for (const auto& c : cands) dup |= c.ctas_per_sm == ctas && c.wave_tiles == wt && c.ws == ws;
       if (dup) continue;
       // the interleaved layout is a candidate only when asked for
       // (DVNR_INTERLEAVE=1): measured slower on both workloads, its trials
       // would only lengthen the first call
       const bool il = interleave_env == 1 && !base.sched;  // needs every model in every step
-      cands.push_back({ctas, wt, il});
+      cands.push_back({ctas, wt, il, ws});
     }
-    if (ctas == 1) break;
+  };
+  if (!only_ws) {
+    for (int ctas = base.lay.ctas_per_sm; ctas >= 1; ctas = ctas > 1 ? 1 : 0) {
+      MpParams q = base;
+      q.lay.ctas_per_sm = ctas;
+      add(q, ctas, false);
+      if (ctas == 1) break;
+    }
   }
-  if (cands.empty()) cands.push_back({base.lay.ctas_per_sm, base.total_tiles, false});
+  if (lay_ws) {
+    MpParams q = base;
+    q.lay = *lay_ws;
+    add(q, 1, true);
+  }
+  if (cands.empty()) cands.push_back({base.lay.ctas_per_sm, base.total_tiles, false, false});
   AdamHyper hd = h;
   hd.dry = 1;
   const int64_t n_store = models[0]->n_store;
@@ -1188,6 +1761,7 @@ dvnr_status autotune(MpParams base, dvnr_model* models, int n, int W, int F, con
   dvnr_status rc = DVNR_OK;
   for (const auto& c : cands) {
     MpParams q = base;
+    if (c.ws) q.lay = *lay_ws;
     q.lay.ctas_per_sm = c.ctas_per_sm;
     set_wave_tiles(q, c.wave_tiles);
     if ((rc = step(q, c.interleaved)) != DVNR_OK) break;  // warm-up
@@ -1458,8 +2032,14 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     const char* at = getenv("DVNR_AUTOTUNE");
     const bool tune = !(at && atoi(at) == 0) && !getenv("DVNR_WAVE_MODELS") && !getenv("DVNR_WAVE_TILES") &&
                       !profiling_on() && p.first_wait_cycles == kWaitCycles;
-    const std::string key = tune_key(m0, n, cfg) + (p.sched ? ":s" : ":u");
-    TuneChoice ch{0, 0, false};
+    // the warp-specialised kernel only when asked for (DVNR_TRAIN_WS=1),
+    // where its layout fits: measured as fast as the plain kernel on the
+    // 256^3 workload, not faster, its trials would only lengthen first calls
+    const int ws_env = train_ws_env();
+    MpLayout lay_ws;
+    const bool ws_ok = ws_env == 1 && make_layout_ws(m0, lay_ws);
+    const std::string key = tune_key(m0, n, cfg) + (p.sched ? ":s" : ":u") + ":ws" + std::to_string(ws_env);
+    TuneChoice ch{0, 0, false, false};
     bool have = false;
     if (tune) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1472,23 +2052,27 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
     if (tune && !have) {
       const int W0 = m0->mlp.width, F0 = m0->lv.F;
       DVNR_WF_DISPATCH(W0, F0, set_smem_attr, true, lay.smem_bytes);
-      dvnr_status rc = autotune(p, models, n, W0, F0, c->d_adam, h, interleave_env, &ch, s);
+      dvnr_status rc = autotune(p, models, n, W0, F0, c->d_adam, h, interleave_env, ws_ok ? &lay_ws : nullptr,
+                                ws_ok && ws_env == 1, &ch, s);
       if (rc != DVNR_OK) return rc;
       std::lock_guard<std::mutex> lk(g_tune_mu);
       g_tune[key] = ch;
       have = true;
     }
     if (have) {
+      if (ch.ws) p.lay = lay_ws;
       p.lay.ctas_per_sm = ch.ctas_per_sm;
       set_wave_tiles(p, ch.wave_tiles);
       interleaved = ch.interleaved && !p.sched;
     } else {
+      if (ws_ok && ws_env == 1) p.lay = lay_ws;
       set_waves(p, m0, n);
       interleaved = interleave_env == 1 && !p.sched;
     }
   }
+  const bool ws = p.lay.ws != 0;
   if (c->any_graph() && (c->wave_tiles != p.wave_tiles || c->ctas_per_sm != p.lay.ctas_per_sm ||
-                  c->scheduled != (p.sched != nullptr) || c->interleaved != interleaved)) {
+                  c->scheduled != (p.sched != nullptr) || c->interleaved != interleaved || c->ws != ws)) {
     DVNR_CUDA(cudaStreamSynchronize(s));
     c->drop_graph();
   }
@@ -1496,6 +2080,7 @@ dvnr_status mp_train(dvnr_model* models, int n, const float* const* vols, const 
   c->ctas_per_sm = p.lay.ctas_per_sm;
   c->scheduled = p.sched != nullptr;
   c->interleaved = interleaved;
+  c->ws = ws;
   const int W = m0->mlp.width, F = m0->lv.F;
   DVNR_WF_DISPATCH(W, F, set_smem_attr, true, lay.smem_bytes);
   auto one_step = [&](cudaStream_t st) -> dvnr_status {
@@ -1528,6 +2113,8 @@ dvnr_status mp_train_grad(dvnr_model m, const float* vol, const dvnr_train_cfg* 
     set_error("FP16 path: configuration exceeds shared or tensor memory");
     return DVNR_E_UNSUPPORTED;
   }
+  MpLayout lay_ws;
+  if (train_ws_env() == 1 && make_layout_ws(m, lay_ws)) lay = lay_ws;
   MpModel hm{m->theta16, m->grad, vol, (int32_t)m->dims[0], (int32_t)m->dims[1], (int32_t)m->dims[2],
              0u, m->st};
   MpModel* d = nullptr;
@@ -1581,6 +2168,8 @@ dvnr_status mp_backward(dvnr_model m, const uint32_t* coords, const float* dy, i
     set_error("FP16 path: configuration exceeds shared or tensor memory");
     return DVNR_E_UNSUPPORTED;
   }
+  MpLayout lay_ws;
+  if (train_ws_env() == 1 && make_layout_ws(m, lay_ws)) lay = lay_ws;
   MpModel hm{m->theta16, m->grad, nullptr, (int32_t)m->dims[0], (int32_t)m->dims[1], (int32_t)m->dims[2],
              0u, m->st};
   MpModel* d = nullptr;

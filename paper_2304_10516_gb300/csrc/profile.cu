@@ -61,6 +61,10 @@ std::atomic<int64_t> g_graph_captures{0}, g_graph_replays{0}, g_eager_steps{0};
 void count_graph_capture() { g_graph_captures.fetch_add(1); }
 void count_graph_replay() { g_graph_replays.fetch_add(1); }
 void count_eager_steps(int64_t n) { g_eager_steps.fetch_add(n); }
+// launches of each FP16 training kernel enqueued by the host (a launch made
+// while a graph is captured counts once, its replays not at all)
+std::atomic<int64_t> g_train_plain{0}, g_train_ws{0};
+void count_train_launch(bool ws) { (ws ? g_train_ws : g_train_plain).fetch_add(1); }
 void set_capturing(bool on) { g_capturing = on; }
 
 ProfScope::ProfScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
@@ -126,6 +130,12 @@ int64_t dvnr_launch_count(void) {
   int64_t n = g_launches.load();
   for (unsigned long long* p : g_dev_counters) n += (int64_t)*reinterpret_cast<volatile unsigned long long*>(p);
   return n;
+}
+
+dvnr_status dvnr_train_kernel_stats(int64_t* plain, int64_t* ws) {
+  if (plain) *plain = dvnr::g_train_plain.load();
+  if (ws) *ws = dvnr::g_train_ws.load();
+  return DVNR_OK;
 }
 
 dvnr_status dvnr_graph_stats(int64_t* captures, int64_t* replays, int64_t* eager_steps) {
