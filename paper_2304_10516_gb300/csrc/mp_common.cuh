@@ -121,6 +121,28 @@ __device__ __forceinline__ void red_add<8>(float* p, const float* g) {
   red_add<4>(p + 4, g + 4);
 }
 
+// Two single-precision products / fused multiply-adds in one instruction
+// (mul.rn.f32x2, fma.rn.f32x2 of the sm_100 family); each lane rounds as the
+// scalar operation does, so results are bit-identical to the scalar form.
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+
 // Store F halves of one sample row (features f0 .. f0+F-1, same 16-byte row).
 template <int F>
 __device__ __forceinline__ void st_row(uint8_t* base, uint32_t off, const float* v) {
@@ -236,12 +258,28 @@ __device__ __forceinline__ void encode_to_tile(const LevelTab& lv, const __half*
       for (int f = 0; f < F; ++f) acc[f] = 0.f;
       // w_k = (wx wy) wz, the x-y products formed once for both z
       const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
-      const float wxy[4] = {gx * gy, fx * gy, gx * fy, fx * fy};
+      if constexpr (F == 2) {
+        // the same products and sums, two lanes per instruction
+        const float2 xy01 = fmul2(make_float2(gx, fx), make_float2(gy, gy));  // wxy[0], wxy[1]
+        const float2 xy23 = fmul2(make_float2(gx, fx), make_float2(fy, fy));  // wxy[2], wxy[3]
+        const float2 w2[4] = {fmul2(xy01, make_float2(gz, gz)), fmul2(xy23, make_float2(gz, gz)),
+                              fmul2(xy01, make_float2(fz, fz)), fmul2(xy23, make_float2(fz, fz))};
+        float2 a2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float w = wxy[k & 3] * ((k >> 2) ? fz : gz);
+        for (int k = 0; k < 8; ++k) {
+          const float w = (k & 1) ? w2[k >> 1].y : w2[k >> 1].x;
+          a2 = ffma2(make_float2(w, w), make_float2(v[g][k][0], v[g][k][1]), a2);
+        }
+        acc[0] = a2.x;
+        acc[F - 1] = a2.y;
+      } else {
+        const float wxy[4] = {gx * gy, fx * gy, gx * fy, fx * fy};
 #pragma unroll
-        for (int f = 0; f < F; ++f) acc[f] += w * v[g][k][f];
+        for (int k = 0; k < 8; ++k) {
+          const float w = wxy[k & 3] * ((k >> 2) ? fz : gz);
+#pragma unroll
+          for (int f = 0; f < F; ++f) acc[f] += w * v[g][k][f];
+        }
       }
       st_row<F>(act, tile_off((uint32_t)(l * F), s), acc);
     }
