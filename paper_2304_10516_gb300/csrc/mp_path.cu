@@ -968,9 +968,10 @@ __global__ void __launch_bounds__(3 * kTile, 1) k_mp_train_ws(const __grid_const
       }
       if (!go) break;
       // -- layer 1: dW_0 += dZ_1^T X0 and dL/dX0 = dZ_1 W_0 into slot b's
-      // columns, once the gathering warps have read the slot's previous
+      // columns, once slot b's gathering group has read the slot's previous
       // dL/dX0; the commit on dx[b] hands both the gradient and the free X0
-      // slot to them (no wait here: the next tile's products queue behind)
+      // slot to that group (no wait here: the next tile's products queue
+      // behind these in the tensor core)
       if (lt == 0) {
         bool ok = true;
         if (t >= 2) ok = umma::mbar_wait_bounded(dxfree + b, (use - 1u) & 1u, abort_flag, kWaitCycles);
