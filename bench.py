@@ -230,8 +230,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk, "gpu_launches": int(launches),
         "graph": {"captures_in_timed_region": g1[0] - g0[0], "graph_launches": g1[1] - g0[1],
                   "eager_steps": g1[2] - g0[2],
-                  "layout": "graphs of 32, 16 and 8 steps for the binary digits of the step "
-                            "count; fewer than 8 remaining steps launched directly"},
+                  "layout": "graphs of 32, 16, 8 and 4 steps for the binary digits of the step "
+                            "count; fewer than 4 remaining steps launched directly"},
     }
     if rank != 0:
         return None

@@ -512,9 +512,9 @@ int64_t dvnr_launch_count(void);
 /* How the FP16 grouped training has run its steps since the library was
  * loaded: CUDA graphs captured (each also instantiated), graph launches, and
  * steps launched directly (each pointer may be NULL). A call of n steps
- * replays graphs of 32 steps, then of 16 and 8 for the binary digits of the
- * rest, each captured on its first use for the call's models and settings;
- * fewer than 8 remaining steps run directly, as does every step while
+ * replays graphs of 32 steps, then of 16, 8 and 4 for the binary digits of
+ * the rest, each captured on its first use for the call's models and
+ * settings; fewer than 4 remaining steps run directly, as does every step while
  * profiling or a lowered wait limit is active. The early-stop loop graph
  * counts one launch per call. Host counters, no synchronisation.           */
 dvnr_status dvnr_graph_stats(int64_t* captures, int64_t* replays, int64_t* eager_steps);

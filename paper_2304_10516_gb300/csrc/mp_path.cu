@@ -51,10 +51,12 @@ namespace {
 #endif
 // Step graphs of the grouped training: 2^kMaxGraphLog steps per replay (and
 // per body run of the early-stop loop); the fixed graphs of a call's
-// remaining steps have 2^k steps, k >= kMinGraphLog (fewer steps run eagerly:
-// their capture would cost more than it saves)
+// remaining steps have 2^k steps, k >= kMinGraphLog (fewer steps run
+// eagerly: a graph of one or two steps saves less than its capture costs a
+// one-off call). A call of n steps thus replays graphs for the binary digits
+// of n down to 4, captured the first time they are needed.
 constexpr int kMaxGraphLog = 5;
-constexpr int kMinGraphLog = 3;
+constexpr int kMinGraphLog = 2;
 
 // Limit of each CTA's first tensor-core wait in the training and decoding
 // kernels (dvnr_debug_first_wait); kWaitCycles unless a test lowers it.
