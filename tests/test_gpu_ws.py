@@ -9,9 +9,10 @@ warp-specialised kernel (DVNR_TRAIN_WS=1), checks through the library's
 launch counters that it ran, and reuses the FP16 path's parity tests: one
 step element by element against the oracle's FP16 emulation (configurations
 with two features per level, where the kernel applies), the ragged last
-tile, grouped launches with waves that split models, the 200-step PSNR, the
-first Adam moment against the plain kernel's, and the bounded-wait failure
-path.
+tile, grouped launches with waves that split models, the full-size step of
+the 256^3 workload (batch 2^18) and the 64-partition grouped call, the
+200-step PSNR, the first Adam moment against the plain kernel's, and the
+bounded-wait failure path.
 """
 import ctypes as C
 
@@ -21,7 +22,9 @@ import pytest
 import parity as P
 import test_gpu_autograd as AG
 import test_gpu_failure as FL
+import test_gpu_fullsize as FS
 import test_gpu_mp as MP
+from test_gpu_fullsize import setup  # noqa: F401  (the 256^3 workload's fixture)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -148,3 +151,11 @@ def test_ws_psnr_matches_plain_kernel_on_the_256_model(dv, A, monkeypatch):
 
     p_plain, p_ws = run("0"), run("1")
     assert abs(p_plain - p_ws) < 0.1, (p_plain, p_ws)
+
+
+def test_ws_fullsize_step_matches_oracle(setup):
+    FS.test_fullsize_step_matches_oracle(setup, 1)
+
+
+def test_ws_fullsize_partitioned_workload_losses(setup):
+    FS.test_fullsize_partitioned_workload_losses(setup)
