@@ -641,16 +641,18 @@ bool make_layout_ws(const dvnr_model m, MpLayout& lay) {
   off += wb;
   off = (off + 1023) / 1024 * 1024;
   const uint32_t feat_bytes = 2048 / 8;
-  lay.smem_dz = off;
-  off += (uint32_t)H * W * feat_bytes;
   lay.smem_act = off;
   lay.smem_x0[0] = off;
   lay.smem_x0[1] = off + (uint32_t)D * feat_bytes;
   lay.act_off[0] = 0;
   for (int k = 1; k < H; ++k) lay.act_off[k] = 2u * (uint32_t)D + (uint32_t)(k - 1) * W;
   off += (2u * (uint32_t)D + (uint32_t)(H - 1) * W) * feat_bytes;
-  // the weight-gradient product of dZ_H reads 128 features from its start
-  // (rows past W land in TMEM lanes that are never read)
+  // dZ last: the weight-gradient product of dZ_H reads 128 features from its
+  // start (rows past W land in TMEM lanes that are never read), and the rows
+  // past the dZ tiles are padding here, not X0 slots that the gathering
+  // groups may be writing meanwhile
+  lay.smem_dz = off;
+  off += (uint32_t)H * W * feat_bytes;
   off = std::max(off, lay.smem_dz + ((uint32_t)(H - 1) * W + 128) * feat_bytes);
   lay.smem_tgt = off;
   off += 2 * 128 * 4;
